@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Benchmark of the fused PFB channeliser on GB300.
+
+One step = one pass of the whole hot path (load, convert, FIR, FFT, store)
+over one batch of synthetic input: C=512 channels, T=8 taps, 2^20 output
+spectra of complex int8 input (sigma=16 Gaussian + a tone at channel 101),
+complex FP32 output.  Inputs (1.07 GB) and outputs (4.29 GB) are larger than
+L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  ``value`` is input GSamples/s over all ranks
+(C * spectra / time, the sample rate f_s of Sec. 3); ``roofline`` relates the
+kernel's algorithmic bytes to the measured HBM copy bandwidth; ``e2e`` is the
+same metric through the host-buffer entry point (copies included);
+``cpu_baseline`` is the FP64 oracle on a bounded sample on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PFB input GSamples/s and % of HBM peak at C=512,T=8; fwd+bwd vs fwd time"
+UNIT = "GSamples/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pfb_fwd_c512_t8_ci8_c64.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--in-dtype", default="ci8", choices=["ci8", "ci16", "cf32"])
+    ap.add_argument("--spectra", type=int, default=1 << 20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    v = line.split(":", 1)[1].strip()
+                    return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, target_s: float):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+    import numpy as np
+
+    import oracle
+    from paper_1511_03599_gb300 import synth
+
+    h = w.taps()
+
+    def run(S):
+        x = synth.stream(w.C, S + w.T - 1, w.in_dtype, w.sigma, w.seed, w.tones)
+        t0 = time.perf_counter()
+        oracle.pfb(x, h, w.C, w.T)
+        return time.perf_counter() - t0
+
+    S = 256
+    dt = run(S)
+    S = int(max(256, min(w.S, S * target_s / max(dt, 1e-3))))
+    dt = run(S)
+    cores = os.cpu_count()
+    return {"value": w.C * S / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{S} of {w.S} spectra of {w.name} (FP64 direct FIR + naive O(C^2) DFT, numpy)",
+            "seconds": dt}
+
+
+def run_reference(args, w):
+    """Reference arm: the FP64 oracle (the CPU program the GPU path is checked against)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1511_03599_gb300 import synth  # noqa: F401
+    import numpy as np
+
+    import oracle
+    h = w.taps()
+    S = 2048
+    x = synth.stream(w.C, S + w.T - 1, w.in_dtype, w.sigma, w.seed, w.tones)
+    for _ in range(args.warmup):
+        oracle.pfb(x[: (64 + w.T - 1) * w.C], h, w.C, w.T)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.pfb(x, h, w.C, w.T)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = w.C * S / t / 1e9
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(w.describe(), sample_spectra_per_step=S),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{S} of {w.S} spectra per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_1511_03599_gb300 import synth
+    w = synth.target_workload(args.in_dtype, args.spectra)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1511_03599_gb300 import ppf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # each rank processes its own stream shard of the same shape (weak scaling)
+    x = synth.stream_torch(w.C, w.n_raw, w.in_dtype, w.sigma, w.seed + 7919 * rank, w.tones, device=dev)
+    h = w.taps()
+    plan = ppf.Plan(w.C, w.T, h, w.in_dtype, w.out_dtype)
+    y = plan.empty_output(w.S, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        plan.execute(x, out=y, stream=stream)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.execute(x, out=y, stream=stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier()
+    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    t_step = total_ms / 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+
+    samples = w.C * w.S
+    b_in, b_out = synth.in_bytes_per_sample(w.in_dtype), synth.out_bytes_per_sample(w.out_dtype)
+    alg_bytes = w.C * w.n_raw * b_in + w.C * w.S * b_out + 4 * w.C * w.T
+    value = world * samples / t_step / 1e9
+    kern_s = statistics.mean(per_launch_ms) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / kern_s / 1e9
+    traffic = profiled_traffic()
+
+    # end to end through the host-buffer entry point: H2D + kernel + D2H every step
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        yh = torch.empty(y.shape, dtype=y.dtype).pin_memory()
+        plan.execute_host(xh, out=yh)
+        barrier()
+        n_e2e = max(2, min(5, args.steps))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.execute_host(xh, out=yh)
+        te = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * samples / te / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
+               "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, 2-stream chunk pipeline"}
+        del xh, yh
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(w, args.cpu_seconds)
+        info = plan.info()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(w.describe(), spectra_per_gpu=w.S, parallelism=f"replicas{world}" if world > 1 else "single",
+                           l2="inputs larger than L2: 1.07 GB in + 4.29 GB out per step, no flush",
+                           launch=info),
+            "hbm_frac": achieved / peak,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "pfb_fwd_kernel<512,8,ci8,c64>", "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel_ms": kern_s * 1e3},
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,136 @@
+/*
+ * ppf.h -- C ABI of the GB300 polyphase filter bank (PFB) channeliser.
+ *
+ * Method: Adamek, Novotny & Armour, "A polyphase filter for many-core
+ * architectures" (arXiv:1511.03599).  For a complex stream split into raw
+ * spectra of C channels ("contiguous in channels", Sec. 3.1) the PFB is
+ *
+ *   FIR (Alg. 1, Sec. 3.2):
+ *     y[s][c] = sum_{t=0}^{T-1} h[t*C + c] * x[(s+t)*C + c]
+ *   DFT (Eq. 2, Sec. 2), unnormalised, sign -i, natural bin order:
+ *     Y[s][m] = sum_{c=0}^{C-1} y[s][c] * exp(-2 pi i c m / C)
+ *
+ * for output spectra s = 0 .. n_spectra-1.  Output spectrum s reads raw
+ * spectra s .. s+T-1, so the input holds C*(n_spectra+T-1) samples and there
+ * is no zero-padded history.  Eq. 1 as printed has a garbled index; this
+ * library follows the index convention of Alg. 1-3 (oldest raw spectrum
+ * paired with tap block 0).  A caller wanting the convolution convention
+ * reverses the tap blocks on the host.
+ *
+ * Both steps run in one CUDA kernel on one GPU (sm_103a); the filtered
+ * spectra y never leave the SM.  Accumulation is FP32 throughout.
+ *
+ * Conventions of every entry point:
+ *   - status codes only: nothing throws, exits or traps;
+ *   - device pointers are caller-owned, must be 16-byte aligned and must not
+ *     overlap; host pointers are read during the call only;
+ *   - work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising, except where noted;
+ *   - a plan is bound to the device that was current when it was made.
+ */
+#ifndef PPF_H
+#define PPF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Input sample types: complex, interleaved (re, im) (Sec. 3.1 input precisions).
+ * Integers are two's complement; the value is the integer, no offset or scale. */
+typedef enum {
+    PPF_IN_CI8 = 0,   /* 2 bytes per sample: int8 re, int8 im   */
+    PPF_IN_CI16 = 1,  /* 4 bytes per sample: int16 re, int16 im */
+    PPF_IN_CF32 = 2   /* 8 bytes per sample: float re, float im */
+} ppf_in_t;
+
+/* Output sample types: complex FP32 (8 bytes) or complex FP16 (4 bytes,
+ * interleaved half re, half im; round-to-nearest-even from the FP32 result,
+ * +-inf on overflow).  The paper always writes 32-bit outputs (Sec. 3.1);
+ * FP16 is an extension. */
+typedef enum {
+    PPF_OUT_CF32 = 0,
+    PPF_OUT_CF16 = 1
+} ppf_out_t;
+
+typedef enum {
+    PPF_OK = 0,
+    PPF_ERR_INVALID_ARG = 1,     /* null pointer, C<1, T<1, n_spectra<1, overlap, bad handle */
+    PPF_ERR_UNSUPPORTED = 2,     /* C not a power of two in [32, 4096], T > 64, unknown dtype */
+    PPF_ERR_ALIGNMENT = 3,       /* a buffer is not 16-byte aligned */
+    PPF_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed */
+    PPF_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up (see ppf_device_status) */
+    PPF_ERR_OUT_OF_MEMORY = 6    /* a device or pinned-host allocation failed */
+} ppf_status;
+
+typedef struct ppf_plan_s* ppf_plan_t;
+typedef void* ppf_stream_t;     /* cudaStream_t */
+
+/* Largest supported values. */
+#define PPF_MIN_CHANNELS 32
+#define PPF_MAX_CHANNELS 4096
+#define PPF_MAX_TAPS 64
+
+/*
+ * ppf_plan -- validate (C, T, types), copy the C*T FP32 coefficients to
+ * device memory owned by the plan and pick the kernel for the shapes.
+ *   out        : receives the plan handle (set to NULL on failure)
+ *   C          : channels per spectrum, a power of two in [32, 4096] (Sec. 2;
+ *                the paper needs C divisible by 32, Sec. 4.1)
+ *   T          : taps, 1 <= T <= 64
+ *   coeffs_host: C*T host floats, tap-major: coeffs_host[t*C + c] is tap t of
+ *                channel c (coefficients are unique per channel and tap and
+ *                always FP32, Sec. 3.1).  Read during the call only.
+ * Allocates device memory (cudaMalloc); synchronous.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA, OUT_OF_MEMORY.
+ */
+ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeffs_host,
+                    ppf_in_t in_dtype, ppf_out_t out_dtype);
+
+/*
+ * ppf_execute -- enqueue the fused FIR + DFT on `stream`.
+ *   in_dev   : device buffer of C*(n_spectra+T-1) input samples (in_dtype)
+ *   out_dev  : device buffer of n_spectra*C output samples (out_dtype),
+ *              spectrum-major: out[s*C + m] = Y[s][m]
+ *   n_spectra: output spectra, >= 1
+ * A long stream is processed in chunks that overlap by T-1 raw spectra.
+ * Asynchronous; one kernel launch; no allocation.
+ * Errors: INVALID_ARG, ALIGNMENT, CUDA (launch failure).
+ */
+ppf_status ppf_execute(ppf_plan_t plan, const void* in_dev, void* out_dev,
+                       long long n_spectra, ppf_stream_t stream);
+
+/*
+ * ppf_execute_host -- the same transform with HOST input and output buffers.
+ * The stream is cut into chunks that are copied host->device, transformed
+ * and copied device->host on a small pipeline of CUDA streams so that the
+ * copies of chunk i+1 and i-1 overlap the compute of chunk i (the copy /
+ * compute overlap of Sec. 5).  Device staging buffers are allocated on the
+ * first call and kept by the plan.  Pinned host buffers give full copy speed;
+ * pageable ones work but are slower.  Synchronous: returns when `out_host`
+ * holds the result.  `stream` orders the call after earlier work on it.
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY.
+ */
+ppf_status ppf_execute_host(ppf_plan_t plan, const void* in_host, void* out_host,
+                            long long n_spectra, ppf_stream_t stream);
+
+/* ppf_destroy -- free the plan and its device memory (synchronises the device
+ * work of the plan's own streams).  NULL is accepted. */
+ppf_status ppf_destroy(ppf_plan_t plan);
+
+/* Human-readable name of a status code (static string). */
+const char* ppf_status_string(ppf_status s);
+
+/* Detail of the last error raised on the calling thread (static buffer). */
+const char* ppf_last_error_message(void);
+
+/* Plan introspection: launch shape chosen for the plan.
+ *   info[0]=threads per CTA, info[1]=spectra per CTA batch, info[2]=grid
+ *   (CTAs), info[3]=dynamic shared memory bytes, info[4]=tap bucket (T
+ *   rounded up), info[5]=number of FFT stages, info[6]=kernel variant. */
+ppf_status ppf_plan_info(ppf_plan_t plan, int info[8]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPF_H */

@@ -1,0 +1,308 @@
+// ppf_abi.cu -- the C ABI declared in include/ppf.h: plan validation, kernel
+// selection, device tables, launches, the host-buffer pipeline and errors.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/ppf.h"
+#include "ppf_fwd.cuh"
+#include "ppf_internal.h"
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+ppf_status fail(ppf_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ppf_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(PPF_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PPF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr uint32_t kMagic = 0x50504631u;   // "PPF1"
+
+int tap_bucket(int T) {
+    if (T <= 1) return 1;
+    if (T <= 2) return 2;
+    if (T <= 4) return 4;
+    if (T <= 8) return 8;
+    if (T <= 16) return 16;
+    return 64;
+}
+
+bool lookup(int C, int tm, int in, int out, ppf::FwdEntry* e) {
+    switch (C) {
+        case 32: return ppf::fwd_lookup_c32(tm, in, out, e);
+        case 64: return ppf::fwd_lookup_c64(tm, in, out, e);
+        case 128: return ppf::fwd_lookup_c128(tm, in, out, e);
+        case 256: return ppf::fwd_lookup_c256(tm, in, out, e);
+        case 512: return ppf::fwd_lookup_c512(tm, in, out, e);
+        case 1024: return ppf::fwd_lookup_c1024(tm, in, out, e);
+        case 2048: return ppf::fwd_lookup_c2048(tm, in, out, e);
+        case 4096: return ppf::fwd_lookup_c4096(tm, in, out, e);
+        default: return false;
+    }
+}
+
+bool twiddles(int C, std::vector<float>& pairs) {
+    int n = 0;
+    switch (C) {
+#define PPF_TW(CC) case CC: n = ppf::fwd_twiddle_count_c##CC(); pairs.assign(2 * n, 0.f); ppf::fwd_twiddles_c##CC(pairs.data()); return true;
+        PPF_TW(32) PPF_TW(64) PPF_TW(128) PPF_TW(256) PPF_TW(512) PPF_TW(1024) PPF_TW(2048) PPF_TW(4096)
+#undef PPF_TW
+        default: return false;
+    }
+}
+
+int bytes_in(ppf_in_t t) { return t == PPF_IN_CI8 ? 2 : t == PPF_IN_CI16 ? 4 : 8; }
+int bytes_out(ppf_out_t t) { return t == PPF_OUT_CF32 ? 8 : 4; }
+
+}  // namespace
+
+// Host pipeline state of ppf_execute_host (allocated on first use).
+struct HostPipe {
+    static constexpr int kDepth = 2;
+    long long chunk = 0;                 // output spectra per chunk
+    cudaStream_t st[kDepth] = {nullptr, nullptr};
+    void* d_in[kDepth] = {nullptr, nullptr};
+    void* d_out[kDepth] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr;
+};
+
+struct ppf_plan_s {
+    uint32_t magic;
+    int C, T, TM, device, grid, sms, occupancy;
+    ppf_in_t in;
+    ppf_out_t out;
+    float* d_taps;        // TM*C floats, rows >= T zero
+    float2* d_tw;         // twiddle tables
+    ppf::FwdEntry fwd;
+    HostPipe* pipe;
+};
+
+// Registry of live plans: a handle is checked against it before it is
+// dereferenced, so a destroyed or foreign handle is rejected, not used.
+static std::mutex g_plans_mu;
+static std::unordered_set<const void*> g_plans;
+
+static bool valid_plan(ppf_plan_t p) {
+    if (p == nullptr) return false;
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    return g_plans.count(p) != 0 && p->magic == kMagic;
+}
+static void register_plan(ppf_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plans.insert(p);
+}
+static void unregister_plan(ppf_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_plans_mu);
+    g_plans.erase(p);
+}
+
+extern "C" const char* ppf_status_string(ppf_status s) {
+    switch (s) {
+        case PPF_OK: return "PPF_OK";
+        case PPF_ERR_INVALID_ARG: return "PPF_ERR_INVALID_ARG";
+        case PPF_ERR_UNSUPPORTED: return "PPF_ERR_UNSUPPORTED";
+        case PPF_ERR_ALIGNMENT: return "PPF_ERR_ALIGNMENT";
+        case PPF_ERR_CUDA: return "PPF_ERR_CUDA";
+        case PPF_ERR_DEVICE_TIMEOUT: return "PPF_ERR_DEVICE_TIMEOUT";
+        case PPF_ERR_OUT_OF_MEMORY: return "PPF_ERR_OUT_OF_MEMORY";
+        default: return "PPF_ERR_UNKNOWN";
+    }
+}
+
+extern "C" const char* ppf_last_error_message(void) { return g_msg; }
+
+extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeffs_host,
+                               ppf_in_t in_dtype, ppf_out_t out_dtype) {
+    if (out == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_plan: out is NULL");
+    *out = nullptr;
+    if (coeffs_host == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_plan: coefficients are NULL");
+    if (C < 1 || T < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_plan: C=%d, T=%d must be >= 1", C, T);
+    if ((C & (C - 1)) != 0 || C < PPF_MIN_CHANNELS || C > PPF_MAX_CHANNELS)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: C=%d is not a power of two in [%d, %d]", C,
+                    PPF_MIN_CHANNELS, PPF_MAX_CHANNELS);
+    if (T > PPF_MAX_TAPS) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: T=%d > %d", T, PPF_MAX_TAPS);
+    if (in_dtype < PPF_IN_CI8 || in_dtype > PPF_IN_CF32)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: unknown input type %d", (int)in_dtype);
+    if (out_dtype < PPF_OUT_CF32 || out_dtype > PPF_OUT_CF16)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: unknown output type %d", (int)out_dtype);
+
+    const int tm = tap_bucket(T);
+    ppf::FwdEntry e{};
+    if (!lookup(C, tm, (int)in_dtype, (int)out_dtype, &e))
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: no kernel for C=%d T=%d", C, T);
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: cudaGetDevice");
+    int sms = 0;
+    ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: SM count");
+    ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: shared memory attribute");
+    int occ = 0;
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, e.smem);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: occupancy");
+    if (occ < 1) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: kernel does not fit on an SM");
+
+    // Device tables: taps padded to the bucket with zero rows, twiddles.
+    std::vector<float> taps((size_t)tm * C, 0.f);
+    std::memcpy(taps.data(), coeffs_host, sizeof(float) * (size_t)C * T);
+    std::vector<float> tw;
+    twiddles(C, tw);
+
+    ppf_plan_s* p = new (std::nothrow) ppf_plan_s{};
+    if (p == nullptr) return fail(PPF_ERR_OUT_OF_MEMORY, "ppf_plan: host allocation");
+    p->magic = kMagic;
+    p->C = C; p->T = T; p->TM = tm; p->device = dev; p->sms = sms; p->occupancy = occ;
+    p->grid = sms * occ;
+    p->in = in_dtype; p->out = out_dtype; p->fwd = e;
+    register_plan(p);
+    ce = cudaMalloc(&p->d_taps, taps.size() * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_tw, tw.size() * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        ppf_status s = cuda_fail(ce, "ppf_plan: device tables");
+        ppf_destroy(p);
+        return s;
+    }
+    *out = p;
+    return PPF_OK;
+}
+
+static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, void* out_dev, long long n, cudaStream_t st) {
+    ppf::FwdArgs a;
+    a.in = in_dev;
+    a.out = out_dev;
+    a.taps = p->d_taps;
+    a.tw = p->d_tw;
+    a.n_spectra = n;
+    a.T = p->T;
+    const long long nb = (n + p->fwd.batch - 1) / p->fwd.batch;
+    const int grid = (int)(nb < p->grid ? nb : p->grid);
+    cudaError_t ce = p->fwd.launch(a, grid, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute: launch");
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_execute(ppf_plan_t p, const void* in_dev, void* out_dev, long long n_spectra,
+                                  ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: invalid plan");
+    if (in_dev == nullptr || out_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: NULL buffer");
+    if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: n_spectra=%lld < 1", n_spectra);
+    if ((reinterpret_cast<uintptr_t>(in_dev) & 15) || (reinterpret_cast<uintptr_t>(out_dev) & 15))
+        return fail(PPF_ERR_ALIGNMENT, "ppf_execute: buffers must be 16-byte aligned");
+    const unsigned long long in_bytes = (unsigned long long)p->C * (n_spectra + p->T - 1) * bytes_in(p->in);
+    const unsigned long long out_bytes = (unsigned long long)p->C * n_spectra * bytes_out(p->out);
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in_dev), o0 = reinterpret_cast<uintptr_t>(out_dev);
+    if (i0 < o0 + out_bytes && o0 < i0 + in_bytes)
+        return fail(PPF_ERR_INVALID_ARG, "ppf_execute: input and output overlap");
+    return launch_fwd(p, in_dev, out_dev, n_spectra, reinterpret_cast<cudaStream_t>(stream));
+}
+
+static void free_pipe(HostPipe* hp) {
+    if (hp == nullptr) return;
+    for (int i = 0; i < HostPipe::kDepth; ++i) {
+        if (hp->st[i]) { cudaStreamSynchronize(hp->st[i]); cudaStreamDestroy(hp->st[i]); }
+        if (hp->d_in[i]) cudaFree(hp->d_in[i]);
+        if (hp->d_out[i]) cudaFree(hp->d_out[i]);
+    }
+    if (hp->start) cudaEventDestroy(hp->start);
+    delete hp;
+}
+
+extern "C" ppf_status ppf_execute_host(ppf_plan_t p, const void* in_host, void* out_host, long long n_spectra,
+                                       ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_execute_host: invalid plan");
+    if (in_host == nullptr || out_host == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_execute_host: NULL buffer");
+    if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_execute_host: n_spectra=%lld < 1", n_spectra);
+    cudaError_t ce;
+    const int C = p->C, T = p->T, bi = bytes_in(p->in), bo = bytes_out(p->out);
+    if (p->pipe == nullptr) {
+        HostPipe* hp = new (std::nothrow) HostPipe{};
+        if (hp == nullptr) return fail(PPF_ERR_OUT_OF_MEMORY, "ppf_execute_host: host allocation");
+        // ~64 MiB of output per chunk, a whole number of CTA batches
+        long long ch = (64ll << 20) / ((long long)C * bo);
+        ch = ch / p->fwd.batch * p->fwd.batch;
+        if (ch < p->fwd.batch) ch = p->fwd.batch;
+        hp->chunk = ch;
+        ce = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
+        for (int i = 0; i < HostPipe::kDepth && ce == cudaSuccess; ++i) {
+            ce = cudaStreamCreateWithFlags(&hp->st[i], cudaStreamNonBlocking);
+            if (ce == cudaSuccess) ce = cudaMalloc(&hp->d_in[i], (size_t)C * (ch + T - 1) * bi);
+            if (ce == cudaSuccess) ce = cudaMalloc(&hp->d_out[i], (size_t)C * ch * bo);
+        }
+        if (ce != cudaSuccess) {
+            free_pipe(hp);
+            return cuda_fail(ce, "ppf_execute_host: staging buffers");
+        }
+        p->pipe = hp;
+    }
+    HostPipe* hp = p->pipe;
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    ce = cudaEventRecord(hp->start, user);
+    for (int i = 0; i < HostPipe::kDepth && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(hp->st[i], hp->start, 0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: stream ordering");
+    // chunk k on stream k % depth: H2D(k) -> kernel(k) -> D2H(k); the other
+    // stream's copies overlap this stream's kernel.
+    long long k = 0;
+    for (long long s0 = 0; s0 < n_spectra; s0 += hp->chunk, ++k) {
+        const int q = (int)(k % HostPipe::kDepth);
+        const long long n = (n_spectra - s0 < hp->chunk) ? n_spectra - s0 : hp->chunk;
+        const char* src = static_cast<const char*>(in_host) + (size_t)s0 * C * bi;
+        char* dst = static_cast<char*>(out_host) + (size_t)s0 * C * bo;
+        ce = cudaMemcpyAsync(hp->d_in[q], src, (size_t)C * (n + T - 1) * bi, cudaMemcpyHostToDevice, hp->st[q]);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: host->device copy");
+        ppf_status s = launch_fwd(p, hp->d_in[q], hp->d_out[q], n, hp->st[q]);
+        if (s != PPF_OK) return s;
+        ce = cudaMemcpyAsync(dst, hp->d_out[q], (size_t)C * n * bo, cudaMemcpyDeviceToHost, hp->st[q]);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: device->host copy");
+    }
+    for (int i = 0; i < HostPipe::kDepth; ++i) {
+        ce = cudaStreamSynchronize(hp->st[i]);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: synchronise");
+    }
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_destroy(ppf_plan_t p) {
+    if (p == nullptr) return PPF_OK;
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_destroy: invalid plan");
+    unregister_plan(p);
+    free_pipe(p->pipe);
+    if (p->d_taps) cudaFree(p->d_taps);
+    if (p->d_tw) cudaFree(p->d_tw);
+    p->magic = 0;
+    delete p;
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_plan_info(ppf_plan_t p, int info[8]) {
+    if (!valid_plan(p) || info == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_plan_info: invalid argument");
+    info[0] = p->fwd.threads;
+    info[1] = p->fwd.batch;
+    info[2] = p->grid;
+    info[3] = p->fwd.smem;
+    info[4] = p->TM;
+    info[5] = p->fwd.stages;
+    info[6] = 0;
+    info[7] = p->occupancy;
+    return PPF_OK;
+}

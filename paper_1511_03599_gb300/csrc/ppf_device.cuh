@@ -1,0 +1,214 @@
+// ppf_device.cuh -- device building blocks of the fused PFB kernels (sm_103a).
+//
+// * compile-time twiddles: cos/sin of 2*pi*k/N evaluated in FP64 by a Taylor
+//   series at compile time and rounded once to FP32;
+// * in-register C-point DFT building block dft_reg<N> (radix-4 / radix-2
+//   decimation in frequency, natural order in and out);
+// * loads of a channel pair for each input type with the int -> FP32
+//   conversion fused in;
+// * streaming stores of complex FP32 / FP16 output.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+
+namespace ppf {
+
+// ---------------------------------------------------------------- utilities
+
+template <int... Is> struct iseq {};
+template <int N, int... Is> struct make_iseq_t : make_iseq_t<N - 1, N - 1, Is...> {};
+template <int... Is> struct make_iseq_t<0, Is...> { using type = iseq<Is...>; };
+template <int I> struct ic { static constexpr int value = I; };
+
+// static_for<N>(f): calls f(ic<0>{}), ..., f(ic<N-1>{}) with compile-time indices.
+template <class F, int... Is>
+__device__ __forceinline__ void static_for_impl(F&& f, iseq<Is...>) {
+    (f(ic<Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, typename make_iseq_t<N>::type{});
+}
+
+constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ------------------------------------------------------ compile-time trig
+// sin(x) for x in [0, pi/4] by its Taylor series, enough terms for FP64.
+constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x * x / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 1; n < 14; ++n) {
+        term *= -x * x / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// cos and sin of 2*pi*k/n for integers, with the octant reduction done on
+// the integer 8k mod 8n so the Taylor argument stays in [0, pi/4].
+constexpr double cos2pi(long k, long n) {
+    k %= n; if (k < 0) k += n;
+    long e = 8 * k;               // angle = (2 pi / (8n)) * e
+    long oct = e / n;             // octant 0..7
+    long r = e - oct * n;         // remainder: angle within octant = 2 pi r / (8 n)
+    double a = 2.0 * kPi * (double)r / (8.0 * (double)n);   // [0, pi/4)
+    double b = kPi / 4.0 - a;                                // for odd octants
+    switch (oct) {
+        case 0: return taylor_cos(a);
+        case 1: return taylor_sin(b);
+        case 2: return -taylor_sin(a);
+        case 3: return -taylor_cos(b);
+        case 4: return -taylor_cos(a);
+        case 5: return -taylor_sin(b);
+        case 6: return taylor_sin(a);
+        default: return taylor_cos(b);
+    }
+}
+constexpr double sin2pi(long k, long n) { return cos2pi(4 * k - n, 4 * n); }  // sin x = cos(x - pi/2)
+
+// W_N^m = exp(-2 pi i m / N) as FP32 constants.
+template <int M, int N> struct Tw {
+    static constexpr float re = (float)cos2pi(M, N);
+    static constexpr float im = (float)(-sin2pi(M, N));
+};
+
+// ---------------------------------------------------------- complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * w for a runtime twiddle w
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+    return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+// a * (-i)
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// a * W_N^M with the trivial cases folded at compile time.
+template <int M, int N>
+__device__ __forceinline__ float2 cmul_tw(float2 a) {
+    constexpr int m = ((M % N) + N) % N;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (4 * m == N) {                 // -i
+        return make_float2(a.y, -a.x);
+    } else if constexpr (2 * m == N) {                 // -1
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (4 * m == 3 * N) {             // +i
+        return make_float2(-a.y, a.x);
+    } else if constexpr (8 * m == N) {                 // (1 - i)/sqrt2
+        constexpr float r = Tw<1, 8>::re;
+        return make_float2((a.x + a.y) * r, (a.y - a.x) * r);
+    } else if constexpr (8 * m == 3 * N) {             // (-1 - i)/sqrt2
+        constexpr float r = Tw<1, 8>::re;
+        return make_float2((a.y - a.x) * r, -(a.x + a.y) * r);
+    } else {
+        constexpr float wr = Tw<m, N>::re, wi = Tw<m, N>::im;
+        return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
+    }
+}
+
+// ------------------------------------------------------- in-register DFT
+constexpr int bitrev(int k, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) { r = (r << 1) | (k & 1); k >>= 1; }
+    return r;
+}
+
+// One radix-4 DIF butterfly group over a block of length LEN = 4*S at BASE,
+// element j (0 <= J < S): two fused radix-2 DIF stages.
+template <int LEN, int BASE, int J, int N>
+__device__ __forceinline__ void r4_bfly(float2 (&v)[N]) {
+    constexpr int S = LEN / 4;
+    float2 a0 = v[BASE + J], a1 = v[BASE + J + S], a2 = v[BASE + J + 2 * S], a3 = v[BASE + J + 3 * S];
+    float2 p = cadd(a0, a2), q = csub(a0, a2);
+    float2 r = cadd(a1, a3), t = cmul_mi(csub(a1, a3));
+    v[BASE + J] = cadd(p, r);
+    v[BASE + J + S] = cmul_tw<2 * J, LEN>(csub(p, r));
+    v[BASE + J + 2 * S] = cmul_tw<J, LEN>(cadd(q, t));
+    v[BASE + J + 3 * S] = cmul_tw<3 * J, LEN>(csub(q, t));
+}
+
+template <int LEN, int N>
+__device__ __forceinline__ void dif_stage(float2 (&v)[N]) {
+    if constexpr (LEN >= 4) {
+        static_for<N / LEN>([&](auto b) {
+            static_for<LEN / 4>([&](auto j) { r4_bfly<LEN, decltype(b)::value * LEN, decltype(j)::value>(v); });
+        });
+        dif_stage<LEN / 4>(v);
+    } else if constexpr (LEN == 2) {
+        static_for<N / 2>([&](auto b) {
+            constexpr int i = decltype(b)::value * 2;
+            float2 a0 = v[i], a1 = v[i + 1];
+            v[i] = cadd(a0, a1);
+            v[i + 1] = csub(a0, a1);
+        });
+    }
+}
+
+// dft_reg<N>: v[k] <- sum_n v[n] exp(-2 pi i n k / N), natural order in/out.
+template <int N>
+__device__ __forceinline__ void dft_reg(float2 (&v)[N]) {
+    static_assert(is_pow2(N), "radix must be a power of two");
+    if constexpr (N > 1) {
+        dif_stage<N>(v);
+        float2 t[N];
+        static_for<N>([&](auto k) { t[decltype(k)::value] = v[bitrev(decltype(k)::value, ilog2(N))]; });
+        static_for<N>([&](auto k) { v[decltype(k)::value] = t[decltype(k)::value]; });
+    }
+}
+
+// ------------------------------------------------------------ input loads
+// One channel pair (c, c+1) of one raw spectrum: 4 floats (re0, im0, re1, im1).
+enum InType { IN_CI8 = 0, IN_CI16 = 1, IN_CF32 = 2 };
+enum OutType { OUT_CF32 = 0, OUT_CF16 = 1 };
+
+template <int IN> struct InTraits;
+template <> struct InTraits<IN_CI8>  { static constexpr int bytes = 2; };
+template <> struct InTraits<IN_CI16> { static constexpr int bytes = 4; };
+template <> struct InTraits<IN_CF32> { static constexpr int bytes = 8; };
+
+__device__ __forceinline__ float4 cvt_ci8x2(uint32_t w) {
+    return make_float4((float)(int8_t)(w & 0xff), (float)(int8_t)((w >> 8) & 0xff),
+                       (float)(int8_t)((w >> 16) & 0xff), (float)(int8_t)(w >> 24));
+}
+__device__ __forceinline__ float4 cvt_ci16x2(uint2 w) {
+    return make_float4((float)(int16_t)(w.x & 0xffff), (float)(int16_t)(w.x >> 16),
+                       (float)(int16_t)(w.y & 0xffff), (float)(int16_t)(w.y >> 16));
+}
+
+// Load the pair at sample offset `off` (even) through the read-only path.
+template <int IN>
+__device__ __forceinline__ float4 load_pair_global(const void* __restrict__ base, long long off) {
+    if constexpr (IN == IN_CI8) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(static_cast<const int8_t*>(base) + 2 * off);
+        return cvt_ci8x2(__ldg(p));
+    } else if constexpr (IN == IN_CI16) {
+        const uint2* p = reinterpret_cast<const uint2*>(static_cast<const int16_t*>(base) + 2 * off);
+        return cvt_ci16x2(__ldg(p));
+    } else {
+        const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(base) + 2 * off);
+        return __ldg(p);
+    }
+}
+
+// ---------------------------------------------------------------- stores
+template <int OUT>
+__device__ __forceinline__ void store_out(void* __restrict__ base, long long idx, float2 v) {
+    if constexpr (OUT == OUT_CF32) {
+        __stcs(reinterpret_cast<float2*>(base) + idx, v);
+    } else {
+        __half2 h = __float22half2_rn(v);
+        __stcs(reinterpret_cast<unsigned int*>(base) + idx, *reinterpret_cast<unsigned int*>(&h));
+    }
+}
+
+}  // namespace ppf

@@ -1,0 +1,37 @@
+// ppf_internal.h -- host-side interface between the C ABI and the per-C
+// kernel instantiation units (one object per channel count C, built from
+// ppf_fwd_inst.cu with -DPPF_C=<C>).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ppf {
+
+struct FwdArgs;
+
+struct FwdEntry {
+    int threads;     // threads per CTA
+    int batch;       // output spectra per CTA batch
+    int smem;        // dynamic shared memory bytes
+    int stages;      // FFT stages
+    int tap_bucket;  // taps rounded up to the compiled bucket
+    const void* fn;  // kernel function (for occupancy queries and attributes)
+    cudaError_t (*launch)(const FwdArgs&, int grid, cudaStream_t);
+};
+
+// Per-C lookups; return false when the (tap bucket, in, out) triple is not built.
+#define PPF_DECLARE_C(C)                                                         \
+    bool fwd_lookup_c##C(int tap_bucket, int in, int out, FwdEntry* e);         \
+    int fwd_twiddle_count_c##C();                                                \
+    void fwd_twiddles_c##C(float* host_pairs);
+PPF_DECLARE_C(32)
+PPF_DECLARE_C(64)
+PPF_DECLARE_C(128)
+PPF_DECLARE_C(256)
+PPF_DECLARE_C(512)
+PPF_DECLARE_C(1024)
+PPF_DECLARE_C(2048)
+PPF_DECLARE_C(4096)
+#undef PPF_DECLARE_C
+
+}  // namespace ppf

@@ -1,0 +1,185 @@
+"""Python binding of the C ABI in ``include/ppf.h`` (ctypes; argument marshalling only).
+
+Every step of the transform runs in the CUDA library ``libppf.so``; PyTorch
+supplies device memory and the current stream.  There is no CPU fallback:
+if the library is missing, every call raises.
+
+    plan = Plan(C=512, T=8, taps=h, in_dtype="ci8", out_dtype="c64")
+    Y = plan(x)            # x: CUDA tensor of C*(S+T-1) samples -> (S, C) complex64
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppf.so")
+
+PPF_OK = 0
+STATUS_NAMES = {0: "PPF_OK", 1: "PPF_ERR_INVALID_ARG", 2: "PPF_ERR_UNSUPPORTED", 3: "PPF_ERR_ALIGNMENT",
+                4: "PPF_ERR_CUDA", 5: "PPF_ERR_DEVICE_TIMEOUT", 6: "PPF_ERR_OUT_OF_MEMORY"}
+IN_CODES = {"ci8": 0, "ci16": 1, "cf32": 2}
+OUT_CODES = {"c64": 0, "c16": 1}
+
+# exported symbols and their ctypes signatures (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "ppf_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                ctypes.c_int, ctypes.c_int]),
+    "ppf_execute": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "ppf_execute_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "ppf_destroy": (ctypes.c_int, [_P]),
+    "ppf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ppf_last_error_message": (ctypes.c_char_p, []),
+    "ppf_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+}
+
+_lib = None
+
+
+class PPFError(RuntimeError):
+    """A non-OK status from the C ABI."""
+
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libppf.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1511_03599_gb300._build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != PPF_OK:
+        msg = lib().ppf_last_error_message()
+        raise PPFError(status, msg.decode() if msg else "")
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+_TORCH_IN = {"ci8": "int8", "ci16": "int16", "cf32": "float32"}
+
+
+def bytes_per_sample(in_dtype: str) -> int:
+    return {"ci8": 2, "ci16": 4, "cf32": 8}[in_dtype]
+
+
+class Plan:
+    """A PFB plan: C channels, T taps, FP32 coefficients h[t*C + c], input/output types."""
+
+    def __init__(self, C: int, T: int, taps, in_dtype: str = "ci8", out_dtype: str = "c64"):
+        if in_dtype not in IN_CODES or out_dtype not in OUT_CODES:
+            raise ValueError(f"unknown dtype pair {in_dtype!r}, {out_dtype!r}")
+        if hasattr(taps, "detach"):
+            taps = taps.detach().cpu().numpy()
+        h = np.ascontiguousarray(np.asarray(taps, dtype=np.float32).reshape(-1))
+        if h.size != C * T:
+            raise ValueError(f"expected {C * T} coefficients, got {h.size}")
+        self.C, self.T, self.in_dtype, self.out_dtype = int(C), int(T), in_dtype, out_dtype
+        self._h = None
+        handle = ctypes.c_void_p()
+        check(lib().ppf_plan(ctypes.byref(handle), self.C, self.T,
+                             h.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             IN_CODES[in_dtype], OUT_CODES[out_dtype]))
+        self._h = handle
+
+    # ------------------------------------------------------------------
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    def info(self) -> dict:
+        a = (ctypes.c_int * 8)()
+        check(lib().ppf_plan_info(self.handle, a))
+        keys = ("threads", "batch", "grid", "smem", "tap_bucket", "fft_stages", "variant", "ctas_per_sm")
+        return dict(zip(keys, list(a)))
+
+    def n_spectra_for(self, x) -> int:
+        """Output spectra for an input tensor/array of interleaved samples."""
+        n_samples = x.numel() if x.is_complex() else x.numel() // 2
+        if n_samples % self.C:
+            raise ValueError("input length is not a whole number of raw spectra")
+        return n_samples // self.C - self.T + 1
+
+    def empty_output(self, n_spectra: int, device=None):
+        import torch
+        if self.out_dtype == "c64":
+            return torch.empty((n_spectra, self.C), dtype=torch.complex64, device=device)
+        return torch.empty((n_spectra, self.C, 2), dtype=torch.float16, device=device)
+
+    def _check_input(self, x):
+        import torch
+        want = getattr(torch, _TORCH_IN[self.in_dtype])
+        ok = x.dtype == want or (self.in_dtype == "cf32" and x.dtype == torch.complex64)
+        if not ok:
+            raise TypeError(f"input dtype {x.dtype} does not match plan input {self.in_dtype}")
+        if not x.is_contiguous():
+            raise ValueError("input must be contiguous")
+
+    def execute(self, x, out=None, stream=None):
+        """Transform the CUDA tensor ``x``; returns (S, C) complex64 or (S, C, 2) float16."""
+        self._check_input(x)
+        if not x.is_cuda:
+            raise ValueError("execute() needs a CUDA tensor; use execute_host() for host buffers")
+        S = self.n_spectra_for(x)
+        if S < 1:
+            raise ValueError(f"input holds fewer than T={self.T} raw spectra")
+        if out is None:
+            out = self.empty_output(S, device=x.device)
+        check(lib().ppf_execute(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                S, _stream_handle(stream)))
+        return out
+
+    __call__ = execute
+
+    def execute_host(self, x, out=None, stream=None):
+        """Transform host buffers (numpy arrays or CPU tensors, pinned for full speed)."""
+        import torch
+        if isinstance(x, np.ndarray):
+            x = torch.from_numpy(np.ascontiguousarray(x))
+        self._check_input(x)
+        if x.is_cuda:
+            raise ValueError("execute_host() takes host buffers")
+        S = self.n_spectra_for(x)
+        if out is None:
+            out = self.empty_output(S, device="cpu")
+        check(lib().ppf_execute_host(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     S, _stream_handle(stream)))
+        return out
+
+    def close(self):
+        if self._h is not None:
+            check(lib().ppf_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

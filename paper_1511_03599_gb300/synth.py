@@ -180,3 +180,31 @@ def sweep_workload(T: int, in_dtype: str, out_dtype: str, S: int = 1 << 18) -> W
     scale = 1.0 / math.sqrt(512) if out_dtype == "c16" else 1.0
     return Workload(f"pfb_c512_t{T}_s{S}_{in_dtype}_{out_dtype}", 512, T, S, in_dtype,
                     out_dtype, sigma, SEED_BASE + 2 + 1000 * ti + di, (), scale)
+
+
+def stream_torch(C: int, n_raw: int, in_dtype: str, sigma: float, seed: int, tones: tuple = (),
+                 device="cuda", chunk: int = 1 << 26):
+    """The ``stream`` recipe drawn with torch's generator on ``device`` (fast for GB-sized
+    benchmark inputs).  Same distribution, quantisation and tones as ``stream``; the
+    random numbers differ from numpy's, so parity tests use ``stream``."""
+    import torch
+    N = int(C) * int(n_raw)
+    tdt = {"ci8": torch.int8, "ci16": torch.int16, "cf32": torch.float32}[in_dtype]
+    out = torch.empty((N, 2), dtype=tdt, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    for lo in range(0, N, chunk):
+        hi = min(N, lo + chunk)
+        z = torch.randn((hi - lo, 2), generator=g, device=device, dtype=torch.float32) * sigma
+        if tones:
+            n = torch.arange(lo, hi, device=device, dtype=torch.int64)
+            for k0, amp in tones:
+                ph = ((n * int(k0)) % C).to(torch.float32) * (2.0 * math.pi / C)
+                z[:, 0] += amp * torch.cos(ph)
+                z[:, 1] += amp * torch.sin(ph)
+        if in_dtype == "cf32":
+            out[lo:hi] = z
+        else:
+            lim = _IN_LIMIT[in_dtype]
+            out[lo:hi] = torch.clamp(torch.round(z), -lim, lim).to(tdt)
+    return out

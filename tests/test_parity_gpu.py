@@ -1,0 +1,215 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 error of the whole compared output against the FP64
+oracle): <= 1e-5 for complex FP32 output, <= 2e-3 for complex FP16 output.
+Sizes span several CTA batches and a ragged tail; the full-size workloads
+are checked on sampled spectra (first T, last T and seeded random ones).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_03599_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "c16": 2e-3}
+SIGMA = {"ci8": 16.0, "ci16": 2000.0, "cf32": 1.0}
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_03599_gb300 import ppf as m
+    m.lib()
+    return m
+
+
+def to_device(x_raw):
+    return torch.from_numpy(np.ascontiguousarray(x_raw)).cuda()
+
+
+def out_to_numpy(y, out_dtype):
+    y = y.cpu()
+    if out_dtype == "c64":
+        return y.numpy().astype(np.complex128)
+    a = y.float().numpy()
+    return a[..., 0].astype(np.float64) + 1j * a[..., 1].astype(np.float64)
+
+
+def run_case(ppf, C, T, S, in_dtype, out_dtype, seed, taps=None, tones=()):
+    scale = 1.0 / np.sqrt(C) if out_dtype == "c16" else 1.0
+    h = synth.design_taps(C, T, scale=scale) if taps is None else taps
+    x = synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], seed, tones)
+    with ppf.Plan(C, T, h, in_dtype, out_dtype) as plan:
+        y = plan(to_device(x))
+        torch.cuda.synchronize()
+    got = out_to_numpy(y, out_dtype)
+    ref = oracle.pfb(x, h, C, T)
+    assert got.shape == ref.shape
+    assert np.all(np.isfinite(got))
+    err = oracle.rel_l2(got, ref)
+    assert err <= TOL[out_dtype], f"C={C} T={T} S={S} {in_dtype}->{out_dtype}: rel L2 {err:.3e}"
+    return got, ref
+
+
+# every channel count, several tap counts (bucket edges and a runtime tap loop),
+# ragged spectrum counts that span several CTA batches
+@pytest.mark.parametrize("C", [32, 64, 128, 256, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("T", [1, 3, 8, 17, 64])
+def test_parity_channels_taps_ci8(ppf, C, T):
+    S = max(3, 24576 // C) + 5
+    run_case(ppf, C, T, S, "ci8", "c64", seed=1000 + C + T)
+
+
+@pytest.mark.parametrize("in_dtype", ["ci8", "ci16", "cf32"])
+@pytest.mark.parametrize("out_dtype", ["c64", "c16"])
+@pytest.mark.parametrize("T", [2, 4, 8, 16, 32, 64])
+def test_parity_types_c512(ppf, in_dtype, out_dtype, T):
+    run_case(ppf, 512, T, 77, in_dtype, out_dtype, seed=2000 + T)
+
+
+@pytest.mark.parametrize("S", [1, 2, 15, 16, 17, 31, 33, 250])
+def test_parity_ragged_spectrum_counts(ppf, S):
+    run_case(ppf, 512, 8, S, "ci8", "c64", seed=3000 + S)
+
+
+@pytest.mark.parametrize("C", [32, 4096])
+def test_parity_single_spectrum_extremes(ppf, C):
+    run_case(ppf, C, 64, 1, "cf32", "c64", seed=3100 + C)
+    run_case(ppf, C, 1, 1, "ci16", "c64", seed=3200 + C)
+
+
+def test_parity_small_workload_full(ppf):
+    """C=256, T=8, 4096 spectra, c64 noise + tone at channel 37: every output compared."""
+    w = synth.small_parity_workload()
+    x = w.input()
+    h = w.taps()
+    with ppf.Plan(w.C, w.T, h, w.in_dtype, w.out_dtype) as plan:
+        got = out_to_numpy(plan(to_device(x)), "c64")
+    ref = oracle.pfb(x, h, w.C, w.T)
+    assert oracle.rel_l2(got, ref) <= TOL["c64"]
+    assert int(np.argmax(np.abs(got).mean(axis=0))) == 37
+
+
+def test_integer_extremes(ppf):
+    """int8 -128 / +127 and int16 -32768 / +32767 are converted exactly."""
+    C, T, S = 64, 4, 40
+    h = synth.design_taps(C, T)
+    rng = np.random.default_rng(5)
+    for dt, lo, hi in (("ci8", -128, 127), ("ci16", -32768, 32767)):
+        x = rng.choice(np.array([lo, hi, 0, -1]), size=(C * (S + T - 1), 2)).astype(np.int8 if dt == "ci8" else np.int16)
+        with ppf.Plan(C, T, h, dt, "c64") as plan:
+            got = out_to_numpy(plan(to_device(x)), "c64")
+        assert oracle.rel_l2(got, oracle.pfb(x, h, C, T)) <= TOL["c64"]
+
+
+def test_impulse_gives_polyphase_branch(ppf):
+    """Impulse at (raw r, channel c0): Y[s][m] = h[(r-s)C + c0] exp(-2 pi i c0 m / C)."""
+    C, T, S, r, c0 = 512, 8, 40, 20, 101
+    h = synth.design_taps(C, T)
+    x = synth.impulse_stream(C, S + T - 1, "cf32", r, c0)
+    with ppf.Plan(C, T, h, "cf32", "c64") as plan:
+        got = out_to_numpy(plan(to_device(x)), "c64")
+    m = np.arange(C)
+    for s in range(S):
+        t = r - s
+        ref = h[t * C + c0] * np.exp(-2j * np.pi * ((c0 * m) % C) / C) if 0 <= t < T else np.zeros(C)
+        assert np.max(np.abs(got[s] - ref)) <= 1e-6 * max(1.0, np.max(np.abs(h)))
+
+
+def test_deterministic_bitwise(ppf):
+    C, T, S = 512, 8, 300
+    h = synth.design_taps(C, T)
+    x = to_device(synth.stream(C, S + T - 1, "ci8", 16.0, 9))
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        a = plan(x).clone()
+        b = plan(x)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.view_as_real(a), torch.view_as_real(b))
+
+
+def test_streaming_chunks_overlap_by_t_minus_1(ppf):
+    """Two chunks that overlap by T-1 raw spectra reproduce the one-shot output."""
+    C, T, S = 256, 8, 200
+    h = synth.design_taps(C, T)
+    x = synth.stream(C, S + T - 1, "ci16", 2000.0, 10)
+    with ppf.Plan(C, T, h, "ci16", "c64") as plan:
+        full = plan(to_device(x))
+        s1 = 77
+        a = plan(to_device(x[: (s1 + T - 1) * C]))
+        b = plan(to_device(x[s1 * C:]))
+    torch.cuda.synchronize()
+    assert torch.equal(torch.cat([a, b]).view(torch.float32), full.view(torch.float32))
+
+
+def test_execute_host_matches_device(ppf):
+    C, T, S = 512, 8, 5000
+    h = synth.design_taps(C, T)
+    x = synth.stream(C, S + T - 1, "ci8", 16.0, 11)
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        dev = plan(to_device(x)).cpu()
+        host = plan.execute_host(torch.from_numpy(x).pin_memory())
+    assert torch.equal(torch.view_as_real(dev), torch.view_as_real(host))
+
+
+def test_execute_rejects_misaligned_and_overlapping(ppf):
+    C, T = 512, 8
+    h = synth.design_taps(C, T)
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        buf = torch.zeros(C * 40 * 2 + 64, dtype=torch.int8, device="cuda")
+        out = plan.empty_output(33, device="cuda")
+        st = ppf.lib().ppf_execute(plan.handle, ppf.ctypes.c_void_p(buf.data_ptr() + 2),
+                                   ppf.ctypes.c_void_p(out.data_ptr()), 33, None)
+        assert st == 3
+        st = ppf.lib().ppf_execute(plan.handle, ppf.ctypes.c_void_p(out.data_ptr()),
+                                   ppf.ctypes.c_void_p(out.data_ptr()), 33, None)
+        assert st == 1
+        st = ppf.lib().ppf_execute(plan.handle, ppf.ctypes.c_void_p(buf.data_ptr()),
+                                   ppf.ctypes.c_void_p(out.data_ptr()), 0, None)
+        assert st == 1
+
+
+def _sampled_indices(S, T, n_random, seed):
+    rng = np.random.default_rng(seed)
+    idx = set(range(min(S, T))) | set(range(max(0, S - T), S))
+    idx |= set(rng.integers(0, S, n_random).tolist())
+    return np.array(sorted(idx))
+
+
+@pytest.mark.parametrize("in_dtype", ["ci8", "cf32"])
+def test_target_workload_full_size_sampled(ppf, in_dtype):
+    """C=512, T=8, 2^20 spectra in the launch configuration the benchmark uses;
+    sampled outputs against the oracle, plus finiteness of every output."""
+    w = synth.target_workload(in_dtype)
+    x = w.input()
+    h = w.taps()
+    with ppf.Plan(w.C, w.T, h, w.in_dtype, w.out_dtype) as plan:
+        xd = to_device(x)
+        y = plan(xd)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(torch.view_as_real(y)).all())
+        idx = _sampled_indices(w.S, w.T, 2048, 77)
+        got = y[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+    ref = oracle.pfb_spectra(x, h, w.C, w.T, idx)
+    assert oracle.rel_l2(got, ref) <= TOL["c64"]
+
+
+@pytest.mark.parametrize("T", [8, 16, 32, 64])
+@pytest.mark.parametrize("in_dtype,out_dtype", [("ci16", "c64"), ("ci16", "c16"), ("cf32", "c64"), ("cf32", "c16")])
+def test_sweep_cells_sampled(ppf, T, in_dtype, out_dtype):
+    """C=512 tap/precision sweep at 2^18 spectra, sampled against the oracle."""
+    w = synth.sweep_workload(T, in_dtype, out_dtype)
+    x = w.input()
+    h = w.taps()
+    with ppf.Plan(w.C, w.T, h, w.in_dtype, w.out_dtype) as plan:
+        y = plan(to_device(x))
+        torch.cuda.synchronize()
+        idx = _sampled_indices(w.S, w.T, 512, 78)
+        sel = y[torch.from_numpy(idx).cuda()]
+        assert bool(torch.isfinite(sel.float() if out_dtype == "c16" else torch.view_as_real(sel)).all())
+        got = out_to_numpy(sel, out_dtype)
+    ref = oracle.pfb_spectra(x, h, w.C, w.T, idx)
+    assert oracle.rel_l2(got, ref) <= TOL[out_dtype]
