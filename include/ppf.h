@@ -126,8 +126,42 @@ const char* ppf_last_error_message(void);
 /* Plan introspection: launch shape chosen for the plan.
  *   info[0]=threads per CTA, info[1]=spectra per CTA batch, info[2]=grid
  *   (CTAs), info[3]=dynamic shared memory bytes, info[4]=tap bucket (T
- *   rounded up), info[5]=number of FFT stages, info[6]=kernel variant. */
+ *   rounded up), info[5]=number of FFT stages, info[6]=kernel variant
+ *   (bit 0: raw input staged through a TMA ring in shared memory; bit 1:
+ *   twiddles in shared memory), info[7]=CTAs resident per SM. */
 ppf_status ppf_plan_info(ppf_plan_t plan, int info[8]);
+
+/*
+ * ppf_check_device -- read (and clear) the plan's device status word after
+ * the work queued on `stream`.  Every device-side wait of the kernels is
+ * bounded; one that gives up makes its CTA return early and sets the word.
+ * Synchronises `stream`.  Returns PPF_OK or PPF_ERR_DEVICE_TIMEOUT (the
+ * outputs of the affected launch are then incomplete); the context stays
+ * usable.  Errors: INVALID_ARG, CUDA.
+ */
+ppf_status ppf_check_device(ppf_plan_t plan, ppf_stream_t stream);
+
+/*
+ * ppf_set_debug_flags -- testing aid.  flags = 1 makes every later launch of
+ * the plan's staged-input kernel wait on a barrier that nothing completes, so
+ * the bounded wait runs out (after 2 ms) and the timeout path is exercised
+ * without faulting the GPU; flags = 0 restores normal operation.
+ * Errors: INVALID_ARG.
+ */
+ppf_status ppf_set_debug_flags(ppf_plan_t plan, int flags);
+
+/*
+ * ppf_probe_rates -- throughput micro-benchmarks of the current device, the
+ * analogue of the paper's type-conversion and bandwidth micro-benchmarks
+ * (Sec. 4.1, Table 3).  Writes up to n rates, in operations per second:
+ *   [0] scalar FP32 FMA, [1] packed f32x2 FMA (two per instruction),
+ *   [2] int8 -> FP32 conversions (compiler conversion instruction),
+ *   [3] int8 -> FP32 conversions by exponent-bias byte placement,
+ *   [4] int16 -> FP32 conversions.
+ * Synchronous (legacy default stream); allocates a small device buffer.
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY.
+ */
+ppf_status ppf_probe_rates(double* rates, int n);
 
 #ifdef __cplusplus
 }

@@ -90,6 +90,8 @@ struct ppf_plan_s {
     ppf_out_t out;
     float* d_taps;        // TM*C floats, rows >= T zero
     float2* d_tw;         // twiddle tables
+    int* d_err;           // device status word written by bounded waits
+    int debug_flags;      // testing aid: ppf::FwdFlags passed to the kernel
     ppf::FwdEntry fwd;
     HostPipe* pipe;
 };
@@ -176,6 +178,8 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     register_plan(p);
     ce = cudaMalloc(&p->d_taps, taps.size() * sizeof(float));
     if (ce == cudaSuccess) ce = cudaMalloc(&p->d_tw, tw.size() * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->d_err, 16);
+    if (ce == cudaSuccess) ce = cudaMemset(p->d_err, 0, 16);
     if (ce == cudaSuccess) ce = cudaMemcpy(p->d_taps, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) {
@@ -193,8 +197,10 @@ static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, void* out_dev, lo
     a.out = out_dev;
     a.taps = p->d_taps;
     a.tw = p->d_tw;
+    a.err = p->d_err;
     a.n_spectra = n;
     a.T = p->T;
+    a.flags = p->debug_flags;
     const long long nb = (n + p->fwd.batch - 1) / p->fwd.batch;
     const int grid = (int)(nb < p->grid ? nb : p->grid);
     cudaError_t ce = p->fwd.launch(a, grid, st);
@@ -289,6 +295,7 @@ extern "C" ppf_status ppf_destroy(ppf_plan_t p) {
     free_pipe(p->pipe);
     if (p->d_taps) cudaFree(p->d_taps);
     if (p->d_tw) cudaFree(p->d_tw);
+    if (p->d_err) cudaFree(p->d_err);
     p->magic = 0;
     delete p;
     return PPF_OK;
@@ -302,7 +309,30 @@ extern "C" ppf_status ppf_plan_info(ppf_plan_t p, int info[8]) {
     info[3] = p->fwd.smem;
     info[4] = p->TM;
     info[5] = p->fwd.stages;
-    info[6] = 0;
+    info[6] = p->fwd.variant;
     info[7] = p->occupancy;
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_check_device(ppf_plan_t p, ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_check_device: invalid plan");
+    int v = 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t ce = cudaMemcpyAsync(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_check_device");
+    if (v != 0) {
+        ce = cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_check_device: reset");
+        return fail(PPF_ERR_DEVICE_TIMEOUT, "a bounded device-side wait gave up; the launch returned early");
+    }
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_set_debug_flags(ppf_plan_t p, int flags) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: invalid plan");
+    if (flags & ~ppf::FWD_INJECT_TIMEOUT) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: unknown flag");
+    p->debug_flags = flags;
     return PPF_OK;
 }

@@ -50,19 +50,22 @@ constexpr int fft_n(int C, int p) {
     for (int q = p; q < fft_stages(C); ++q) n *= fft_radix(C, q);
     return n;
 }
-// Padded physical index inside one spectrum slot for buffer A_p.
-// A_0 (the FIR output) is unpadded; later buffers get one pad element every
-// G elements so strided column reads do not collide in shared-memory banks.
-constexpr int pad_group(int C, int p) {
-    return p == fft_stages(C) - 1 ? (fft_radix(C, p) > 16 ? fft_radix(C, p) : 16) : 16;
-}
+// Physical index inside one spectrum slot of buffer A_p.  Buffers read by
+// a non-final stage are plain; the buffer read by the last stage (rows of
+// R = R_last elements, read column-wise by lanes walking consecutive rows
+// and written row-wise) is XOR-swizzled within each row so both access
+// patterns hit 16 distinct 8-byte bank pairs per half-warp.
 template <int C, int P>
 __device__ __forceinline__ int phys(int i) {
-    if constexpr (P == 0) return i;
-    else return i + i / pad_group(C, P);
+    constexpr int NST = fft_stages(C);
+    if constexpr (P > 0 && P == NST - 1) {
+        constexpr int R = fft_radix(C, P);
+        constexpr int RPG = R >= 16 ? 1 : 16 / R;   // rows sharing one 16-element bank group
+        return i ^ (((i / R) / RPG) & (R - 1));
+    } else {
+        return i;
+    }
 }
-// Floats2 per spectrum slot (even, so float4 stores of y stay aligned).
-constexpr int slot_size(int C) { return C + C / 16; }
 // Twiddle table offsets: stage p (p < P-1) holds W_{N_p}^{b k} at [k*N_{p+1} + b].
 constexpr int tw_offset(int C, int p) {
     int off = 0;
@@ -82,24 +85,41 @@ struct FwdShape {
     static constexpr int G = B / L;                                  // segments per batch
     static constexpr int FIR_ITEMS = PAIRS * G;                      // (pair, segment) items
     static constexpr int FPT = FIR_ITEMS / NT;                       // FIR items per thread
-    static constexpr int SLOT = slot_size(C);
-    static constexpr int SMEM = (B * SLOT + tw_size(C)) * 8;         // dynamic smem bytes
+    static constexpr int YBYTES = B * C * 8;                         // filtered spectra of a batch
+    static constexpr int TWBYTES = tw_size(C) * 8;
+    static constexpr int BIN = InTraits<IN>::bytes;
+    static constexpr int SLOTB = B * C * BIN;                        // raw bytes of one batch
+    static constexpr int NS = 3;                                     // ring slots
+    static constexpr int CTA_SMEM_MAX = (NT == 256 ? 113 * 1024 : 226 * 1024) - 128;
+    // TMA ring: every raw batch is copied into shared memory once; the FIR of
+    // batch k reads slot k and the T-1 halo rows at the head of slot k+1.
+    static constexpr bool RING = (TM - 1 <= B) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
+    static constexpr bool TW_SMEM = YBYTES + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
+    static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
+    static constexpr int SMEM = RING_OFF + (RING ? NS * SLOTB + 64 : 0);
     // each thread keeps one channel pair for the whole run: taps stay in registers
     static constexpr bool TAPS_IN_REGS = (FPT == 1) && (TM <= 16) && (NT % PAIRS == 0);
     static_assert(FPT * NT == FIR_ITEMS && FPT >= 1, "FIR items must divide evenly");
+    static_assert(SLOTB % 16 == 0 && YBYTES % 16 == 0 && TWBYTES % 16 == 0, "16-byte alignment");
 };
+
+enum FwdFlags { FWD_INJECT_TIMEOUT = 1 };
+constexpr uint64_t kWaitLimitNs = 2000000000ull;     // 2 s
+constexpr uint64_t kInjectedWaitNs = 2000000ull;     // 2 ms
 
 struct FwdArgs {
     const void* in;          // raw stream, C*(n_spectra+T-1) samples
     void* out;               // n_spectra*C outputs
     const float* taps;       // TM*C floats, tap-major, rows >= T are zero
     const float2* tw;        // twiddle tables, tw_size(C) entries
+    int* err;                // device status word: 1 = a bounded wait gave up
     long long n_spectra;
     int T;
+    int flags;               // FwdFlags (testing aid)
 };
 
 // One FFT stage over the whole batch held in shared memory.
-template <int C, int B, int NT, int P, int OUT>
+template <int C, int B, int NT, int P, int OUT, bool TW_SMEM>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long n_spectra) {
     constexpr int NST = fft_stages(C);
@@ -109,7 +129,6 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int PP = C / NP;                 // prefixes at this stage
     constexpr int ITEMS = C / R;               // items per spectrum
     constexpr int IPT = B * ITEMS / NT;        // items per thread
-    constexpr int SLOT = slot_size(C);
     static_assert(IPT * NT == B * ITEMS, "items must divide evenly");
     const int tid = threadIdx.x;
 
@@ -119,7 +138,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         const int item = tid + it * NT;
         const int sp = item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
-        const float2* src = ybuf + sp * SLOT;
+        const float2* src = ybuf + sp * C;
 #pragma unroll
         for (int a = 0; a < R; ++a) v[it][a] = src[phys<C, P>(prefix * NP + NN * a + b)];
     }
@@ -133,8 +152,11 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         if constexpr (P + 1 < NST) {
             const float2* twp = tws + tw_offset(C, P);
 #pragma unroll
-            for (int k = 1; k < R; ++k) v[it][k] = cmul(v[it][k], twp[k * NN + b]);
-            float2* dst = ybuf + sp * SLOT;
+            for (int k = 1; k < R; ++k) {
+                const float2 w = TW_SMEM ? twp[k * NN + b] : __ldg(twp + k * NN + b);
+                v[it][k] = cmul(v[it][k], w);
+            }
+            float2* dst = ybuf + sp * C;
 #pragma unroll
             for (int k = 0; k < R; ++k) dst[phys<C, P + 1>((prefix + PP * k) * NN + b)] = v[it][k];
         } else {
@@ -155,19 +177,39 @@ __device__ __forceinline__ void fma_pair(float4& acc, float2 h, float4 x) {
     acc.w = fmaf(h.y, x.w, acc.w);
 }
 
-template <int C, int IN>
-__device__ __forceinline__ float4 load_raw(const void* in, long long r, long long n_raw, int cp) {
-    return (r < n_raw) ? load_pair_global<IN>(in, r * C + 2 * cp) : make_float4(0.f, 0.f, 0.f, 0.f);
-}
+// Where the FIR reads raw samples of channel pair cp from: rows are relative
+// to the first raw spectrum of the batch (row r feeds outputs r-T+1 .. r).
+template <int C, int IN, bool RING, int B>
+struct RawSrc {
+    static constexpr int BIN = InTraits<IN>::bytes;
+    // ring: shared-memory slots of the batch and of the next batch
+    const unsigned char* cur;
+    const unsigned char* nxt;
+    // direct: global stream
+    const void* in;
+    long long row0, n_raw;
+    int cp;
 
-// FIR (Alg. 1) of channel pair cp for the L output spectra r0 .. r0+L-1:
+    __device__ __forceinline__ float4 load(int r) const {
+        if constexpr (RING) {
+            const unsigned char* p = (r < B) ? cur + (size_t)r * C * BIN : nxt + (size_t)(r - B) * C * BIN;
+            return load_pair_smem<IN>(p);
+        } else {
+            const long long rr = row0 + r;
+            return (rr < n_raw) ? load_pair_global<IN>(in, rr * C + 2 * cp) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+};
+
+// FIR (Alg. 1) of channel pair cp for the L output spectra whose first raw
+// row is r0 (relative to the batch):
 //   acc[j] = sum_{t<T} h[t][cp] * x[r0 + j + t][cp]
 // Every raw sample of the segment (L+T-1 of them) is loaded and converted
 // once; the taps are applied in ascending t for every output.
-template <int C, int TM, int IN, int L, int PAIRS, bool TAPS_IN_REGS>
-__device__ __forceinline__ void fir_segment(const void* __restrict__ in, const float2* __restrict__ taps2,
-                                            const float2 (&hreg)[TAPS_IN_REGS ? TM : 1], int cp,
-                                            long long r0, long long n_raw, int T, float4 (&acc)[L]) {
+template <int TM, int IN, int L, int PAIRS, bool TAPS_IN_REGS, class Src>
+__device__ __forceinline__ void fir_segment(const Src& src, const float2* __restrict__ taps2,
+                                            const float2 (&hreg)[TAPS_IN_REGS ? TM : 1], int cp, int r0,
+                                            int T, float4 (&acc)[L]) {
 #pragma unroll
     for (int j = 0; j < L; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
     if constexpr (TM <= 16) {
@@ -181,7 +223,7 @@ __device__ __forceinline__ void fir_segment(const void* __restrict__ in, const f
 #pragma unroll
         for (int i = 0; i < L + TM - 1; ++i) {
             if (i < L + T - 1) {
-                const float4 x = load_raw<C, IN>(in, r0 + i, n_raw, cp);
+                const float4 x = src.load(r0 + i);
 #pragma unroll
                 for (int j = 0; j < L; ++j) {
                     const int t = i - j;
@@ -197,12 +239,12 @@ __device__ __forceinline__ void fir_segment(const void* __restrict__ in, const f
         }
     } else {
         // Large T: tap-outer order with a circular window of L samples
-        // (slot (i mod L) holds raw sample r0+i), T is a runtime loop bound.
+        // (slot (i mod L) holds raw row r0+i), T is a runtime loop bound.
         // After tap t the sample r0+t is dead and its slot is refilled with
         // r0+t+L, L taps before it is needed.  Live: L accumulators + L samples.
         float4 xw[L];
 #pragma unroll
-        for (int i = 0; i < L; ++i) xw[i] = load_raw<C, IN>(in, r0 + i, n_raw, cp);
+        for (int i = 0; i < L; ++i) xw[i] = src.load(r0 + i);
 #pragma unroll 1
         for (int tb = 0; tb < T; tb += L) {
 #pragma unroll
@@ -212,7 +254,7 @@ __device__ __forceinline__ void fir_segment(const void* __restrict__ in, const f
                     const float2 h = __ldg(taps2 + t * PAIRS + cp);
 #pragma unroll
                     for (int j = 0; j < L; ++j) fma_pair(acc[j], h, xw[(j + u) % L]);
-                    if (t + 1 < T) xw[u] = load_raw<C, IN>(in, r0 + t + L, n_raw, cp);
+                    if (t + 1 < T) xw[u] = src.load(r0 + t + L);
                 }
             }
         }
@@ -223,61 +265,152 @@ template <int C, int TM, int IN, int OUT>
 __global__ void __launch_bounds__(FwdShape<C, TM, IN>::NT, FwdShape<C, TM, IN>::NT == 256 ? 2 : 1)
 pfb_fwd_kernel(FwdArgs args) {
     using S = FwdShape<C, TM, IN>;
-    constexpr int NT = S::NT, B = S::B, L = S::L, SLOT = S::SLOT;
+    constexpr int NT = S::NT, B = S::B, L = S::L, NS = S::NS;
     constexpr int NST = fft_stages(C);
-    extern __shared__ float4 smem_f4[];
-    float2* ybuf = reinterpret_cast<float2*>(smem_f4);
-    float2* tws = ybuf + B * SLOT;
+    constexpr bool RING = S::RING;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* ybuf = reinterpret_cast<float2*>(smem);
+    float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
+    unsigned char* ring = smem + S::RING_OFF;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NS * S::SLOTB);   // NS + 1 barriers
+    volatile int* sflag = reinterpret_cast<volatile int*>(bars + NS + 1);
 
     const int tid = threadIdx.x;
     const long long n_spectra = args.n_spectra;
-    const long long n_raw = n_spectra + args.T - 1;
     const int T = args.T;
-    const long long nbatch = (n_spectra + B - 1) / B;
+    const long long n_raw = n_spectra + T - 1;
+    const long long nbt = (n_spectra + B - 1) / B;
+    // contiguous range of batches per CTA: raw spectra stream through the CTA once
+    const long long lo = (long long)blockIdx.x * nbt / gridDim.x;
+    const long long hi = (long long)(blockIdx.x + 1) * nbt / gridDim.x;
+    const long long nb = hi - lo;
+    if (nb <= 0) return;
 
-    for (int i = tid; i < tw_size(C); i += NT) tws[i] = args.tw[i];
-
-    // FIR work assignment: item = tid + k*NT -> pair cp = item % PAIRS, segment g = item / PAIRS.
+    const float2* tws = args.tw;
+    if constexpr (S::TW_SMEM) {
+        for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
+        tws = tw_s;
+    }
     const float2* taps2 = reinterpret_cast<const float2*>(args.taps);   // [t][pair]
     float2 hreg[S::TAPS_IN_REGS ? TM : 1];
     if constexpr (S::TAPS_IN_REGS) {
 #pragma unroll
         for (int t = 0; t < TM; ++t) hreg[t] = __ldg(taps2 + t * S::PAIRS + tid % S::PAIRS);
     }
-    __syncthreads();
 
-    for (long long batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-        const long long sb = batch * B;             // first output spectrum of the batch
-        // ---------------------------------------------------------- FIR
-#pragma unroll 1
-        for (int k = 0; k < S::FPT; ++k) {
-            const int item = tid + k * NT;
-            const int cp = item % S::PAIRS, g = item / S::PAIRS;
-            const long long r0 = sb + g * L;        // first raw spectrum of the segment
-            float4 acc[L];
-            fir_segment<C, TM, IN, L, S::PAIRS, S::TAPS_IN_REGS>(args.in, taps2, hreg, cp, r0, n_raw, T, acc);
-#pragma unroll
-            for (int j = 0; j < L; ++j)
-                *reinterpret_cast<float4*>(ybuf + (g * L + j) * SLOT + 2 * cp) = acc[j];
+    // ------------------------------------------------------- ring set-up
+    // Relative batch j (0 <= j <= nb; j == nb is the halo-only batch) has
+    // raw rows [(lo+j)*B, (lo+j)*B + B) clipped to the stream.
+    auto rows_of = [&](long long j) -> long long {
+        const long long r = n_raw - (lo + j) * B;
+        return r <= 0 ? 0 : (r < B ? r : B);
+    };
+    const long long last_needed = (T > 1) ? nb : nb - 1;   // last relative batch the FIRs read
+    long long issued = 0, waited = 0;                        // meaningful in thread 0 only
+    auto issue = [&](long long j) {
+        const long long rows = rows_of(j);
+        if (rows > 0) {
+            uint64_t* bar = &bars[j % NS];
+            const uint32_t bytes = (uint32_t)(rows * C * S::BIN);
+            mbar_expect_tx(bar, bytes);
+            tma_load_1d(ring + (j % NS) * S::SLOTB,
+                        static_cast<const unsigned char*>(args.in) + (size_t)(lo + j) * B * C * S::BIN, bytes, bar);
+        }
+    };
+    auto wait_upto = [&](long long j) -> bool {            // thread 0: batches < issued only
+        bool ok = true;
+        for (; waited <= j && waited < issued; ++waited) {
+            if (rows_of(waited) > 0)
+                ok = ok && mbar_wait_bounded(&bars[waited % NS], (uint32_t)((waited / NS) & 1), kWaitLimitNs);
+        }
+        return ok;
+    };
+    if constexpr (RING) {
+        if (tid == 0) {
+            for (int i = 0; i <= NS; ++i) mbar_init(&bars[i], 1);
+            fence_mbar_init();
+            *sflag = 0;
         }
         __syncthreads();
+        if (tid == 0) {
+            for (; issued < NS && issued <= last_needed; ++issued) issue(issued);
+        }
+    }
+    __syncthreads();
+
+    for (long long k = 0; k < nb; ++k) {
+        const long long sb = (lo + k) * B;          // first output spectrum of the batch
+        if constexpr (RING) {
+            if (tid == 0) {
+                bool ok = wait_upto((T > 1) ? k + 1 : k);
+                if (k == 0 && (args.flags & FWD_INJECT_TIMEOUT))  // a barrier nothing arrives on
+                    ok = ok && mbar_wait_bounded(&bars[NS], 0, kInjectedWaitNs);
+                if (!ok) {
+                    // give up: let every copy in flight land, then report
+                    for (; waited < issued; ++waited)
+                        if (rows_of(waited) > 0)
+                            mbar_wait_bounded(&bars[waited % NS], (uint32_t)((waited / NS) & 1), kWaitLimitNs);
+                    atomicExch(args.err, 1);
+                    *sflag = 1;
+                }
+            }
+            __syncthreads();
+            if (*sflag) return;
+        } else {
+            if (tid == 0 && k + 2 < nb) {           // warm L2 two batches ahead
+                const long long r0 = (sb + 2 * B), rows = (n_raw - r0 < B) ? n_raw - r0 : B;
+                if (rows > 0)
+                    tma_prefetch_l2(static_cast<const unsigned char*>(args.in) + (size_t)r0 * C * S::BIN,
+                                    (uint32_t)(rows * C * S::BIN));
+            }
+        }
+        // ---------------------------------------------------------- FIR
+#pragma unroll 1
+        for (int f = 0; f < S::FPT; ++f) {
+            const int item = tid + f * NT;
+            const int cp = item % S::PAIRS, g = item / S::PAIRS;
+            RawSrc<C, IN, RING, B> src;
+            if constexpr (RING) {
+                src.cur = ring + (k % NS) * S::SLOTB + 2 * cp * S::BIN;
+                src.nxt = ring + ((k + 1) % NS) * S::SLOTB + 2 * cp * S::BIN;
+            } else {
+                src.in = args.in;
+                src.row0 = sb;
+                src.n_raw = n_raw;
+                src.cp = cp;
+            }
+            float4 acc[L];
+            fir_segment<TM, IN, L, S::PAIRS, S::TAPS_IN_REGS>(src, taps2, hreg, cp, g * L, T, acc);
+#pragma unroll
+            for (int j = 0; j < L; ++j)
+                *reinterpret_cast<float4*>(ybuf + (g * L + j) * C + 2 * cp) = acc[j];
+        }
+        __syncthreads();
+        if constexpr (RING) {
+            // slot k is free: refill it with batch k+NS
+            if (tid == 0 && issued <= last_needed && issued == k + NS) {
+                fence_proxy_async_smem();
+                issue(issued);
+                ++issued;
+            }
+        }
         // ---------------------------------------------------------- FFT
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT>(ybuf, tws, args.out, sb, n_spectra);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, n_spectra);
         });
     }
 }
 
 // Host side: shape + launch of one instantiation.
 struct FwdInfo {
-    int threads, batch, smem, stages, tap_bucket;
+    int threads, batch, smem, stages, tap_bucket, variant;
     const void* fn;
 };
 
 template <int C, int TM, int IN, int OUT>
 inline FwdInfo fwd_info() {
     using S = FwdShape<C, TM, IN>;
-    return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM,
+    return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, (S::RING ? 1 : 0) | (S::TW_SMEM ? 2 : 0),
                    reinterpret_cast<const void*>(&pfb_fwd_kernel<C, TM, IN, OUT>)};
 }
 

@@ -16,7 +16,7 @@ namespace ppf {
 template <int TM, int IN, int OUT>
 static bool make_entry(FwdEntry* e) {
     FwdInfo i = fwd_info<PPF_C, TM, IN, OUT>();
-    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.fn, &fwd_launch<PPF_C, TM, IN, OUT>};
+    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fwd_launch<PPF_C, TM, IN, OUT>};
     return true;
 }
 

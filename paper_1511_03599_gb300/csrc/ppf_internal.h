@@ -15,6 +15,7 @@ struct FwdEntry {
     int smem;        // dynamic shared memory bytes
     int stages;      // FFT stages
     int tap_bucket;  // taps rounded up to the compiled bucket
+    int variant;     // bit 0: raw input staged by a TMA ring; bit 1: twiddles in shared memory
     const void* fn;  // kernel function (for occupancy queries and attributes)
     cudaError_t (*launch)(const FwdArgs&, int grid, cudaStream_t);
 };

@@ -34,6 +34,9 @@ _SIGS = {
     "ppf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ppf_last_error_message": (ctypes.c_char_p, []),
     "ppf_plan_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "ppf_check_device": (ctypes.c_int, [_P, _P]),
+    "ppf_set_debug_flags": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ppf_probe_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
 }
 
 _lib = None
@@ -167,6 +170,14 @@ class Plan:
                                      S, _stream_handle(stream)))
         return out
 
+    def check_device(self, stream=None):
+        """Synchronise ``stream`` and raise PPFError if a bounded device wait gave up."""
+        check(lib().ppf_check_device(self.handle, _stream_handle(stream)))
+
+    def set_debug_flags(self, flags: int):
+        """Testing aid: 1 makes launches run out a bounded wait (see ppf.h)."""
+        check(lib().ppf_set_debug_flags(self.handle, int(flags)))
+
     def close(self):
         if self._h is not None:
             check(lib().ppf_destroy(self._h))
@@ -183,3 +194,11 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def probe_rates() -> dict:
+    """Device micro-benchmarks (ops/s): FP32 FMA, f32x2 FMA, int8/int16 -> FP32 conversions."""
+    r = (ctypes.c_double * 5)()
+    check(lib().ppf_probe_rates(r, 5))
+    keys = ("ffma", "ffma2", "cvt_s8", "cvt_s8_bias", "cvt_s16")
+    return dict(zip(keys, list(r)))

@@ -168,6 +168,9 @@ def target_workload(in_dtype: str = "ci8", S: int = 1 << 20) -> Workload:
     if in_dtype == "cf32":
         return Workload(f"pfb_c512_t8_s{S}_cf32_c64", 512, 8, S, "cf32", "c64", 1.0,
                         SEED_BASE + 1 + 100, ((101, 2.0),))
+    if in_dtype == "ci16":
+        return Workload(f"pfb_c512_t8_s{S}_ci16_c64", 512, 8, S, "ci16", "c64", 2000.0,
+                        SEED_BASE + 1 + 200, ((101, 4000.0),))
     raise ValueError(in_dtype)
 
 

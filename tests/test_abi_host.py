@@ -85,6 +85,9 @@ def test_execute_and_destroy_reject_bad_handles(L):
     assert L.ppf_destroy(bogus) == 1
     info = (ctypes.c_int * 8)()
     assert L.ppf_plan_info(bogus, info) == 1
+    assert L.ppf_check_device(bogus, None) == 1
+    assert L.ppf_set_debug_flags(bogus, 1) == 1
+    assert L.ppf_probe_rates(None, 5) == 1
 
 
 def test_python_plan_raises_without_device_or_on_bad_args():

@@ -213,3 +213,28 @@ def test_sweep_cells_sampled(ppf, T, in_dtype, out_dtype):
         got = out_to_numpy(sel, out_dtype)
     ref = oracle.pfb_spectra(x, h, w.C, w.T, idx)
     assert oracle.rel_l2(got, ref) <= TOL[out_dtype]
+
+
+def test_bounded_wait_timeout_reported_and_context_usable(ppf):
+    """A wait that nothing completes runs out, is reported, and the next launch is correct."""
+    C, T, S = 512, 8, 4096
+    h = synth.design_taps(C, T)
+    x = synth.stream(C, S + T - 1, "ci8", 16.0, 12)
+    xd = to_device(x)
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        assert plan.info()["variant"] & 1, "expected the TMA-staged kernel for this shape"
+        plan.set_debug_flags(1)
+        plan(xd)
+        with pytest.raises(ppf.PPFError) as ei:
+            plan.check_device()
+        assert ei.value.status == 5
+        plan.set_debug_flags(0)
+        y = plan(xd)
+        plan.check_device()
+        got = out_to_numpy(y, "c64")
+    assert oracle.rel_l2(got, oracle.pfb(x, h, C, T)) <= TOL["c64"]
+
+
+def test_probe_rates(ppf):
+    r = ppf.probe_rates()
+    assert all(v > 1e9 for v in r.values()), r
