@@ -119,9 +119,10 @@ struct FwdArgs {
 };
 
 // One FFT stage over the whole batch held in shared memory.
+// Output spectrum of batch row sp is sb + sp; it is stored when it lies in [vlo, vhi).
 template <int C, int B, int NT, int P, int OUT, bool TW_SMEM>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
-                                          void* __restrict__ out, long long sb, long long n_spectra) {
+                                          void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
     constexpr int R = fft_radix(C, P);
     constexpr int NP = fft_n(C, P);
@@ -161,7 +162,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             for (int k = 0; k < R; ++k) dst[phys<C, P + 1>((prefix + PP * k) * NN + b)] = v[it][k];
         } else {
             const long long s = sb + sp;
-            if (s < n_spectra) {
+            if (s >= vlo && s < vhi) {
 #pragma unroll
                 for (int k = 0; k < R; ++k) store_out<OUT>(out, s * C + prefix + PP * k, v[it][k]);
             }
@@ -396,7 +397,7 @@ pfb_fwd_kernel(FwdArgs args) {
         }
         // ---------------------------------------------------------- FFT
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, n_spectra);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, 0, n_spectra);
         });
     }
 }
@@ -407,17 +408,34 @@ struct FwdInfo {
     const void* fn;
 };
 
+}  // namespace ppf
+
+#include "ppf_fwd_carry.cuh"
+
+namespace ppf {
+
 template <int C, int TM, int IN, int OUT>
 inline FwdInfo fwd_info() {
-    using S = FwdShape<C, TM, IN>;
-    return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, (S::RING ? 1 : 0) | (S::TW_SMEM ? 2 : 0),
-                   reinterpret_cast<const void*>(&pfb_fwd_kernel<C, TM, IN, OUT>)};
+    if constexpr (CarryShape<C, TM, IN>::OK) {
+        using S = CarryShape<C, TM, IN>;
+        return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4,
+                       reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT>)};
+    } else {
+        using S = FwdShape<C, TM, IN>;
+        return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, (S::RING ? 1 : 0) | (S::TW_SMEM ? 2 : 0),
+                       reinterpret_cast<const void*>(&pfb_fwd_kernel<C, TM, IN, OUT>)};
+    }
 }
 
 template <int C, int TM, int IN, int OUT>
 inline cudaError_t fwd_launch(const FwdArgs& a, int grid, cudaStream_t st) {
-    using S = FwdShape<C, TM, IN>;
-    pfb_fwd_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    if constexpr (CarryShape<C, TM, IN>::OK) {
+        using S = CarryShape<C, TM, IN>;
+        pfb_fwd_carry_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    } else {
+        using S = FwdShape<C, TM, IN>;
+        pfb_fwd_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    }
     return cudaPeekAtLastError();
 }
 

@@ -1,0 +1,208 @@
+// ppf_fwd_carry.cuh -- fused PFB forward kernel with the FIR halo carried in
+// registers (used where each thread keeps one channel pair for the whole run).
+//
+// The raw stream of a CTA's contiguous range passes through a double-buffered
+// TMA ring: slot k%2 holds raw spectra [(lo+k)B, (lo+k)B + B).  The T-1 raw
+// spectra an output batch needs from before its slot (the overlap of
+// neighbouring blocks, Sec. 3.2) are the last T-1 rows the same thread
+// converted in the previous batch, kept in registers.  So every raw sample
+// is read from HBM once, copied to shared memory once, loaded and converted
+// by one thread once, and the copy of batch k+1 has a whole batch of compute
+// (FIR k and the FFT of k) to land.  Because of the carry, batch k produces
+// output spectra (lo+k)B - (T-1) .. (lo+k)B + B - T; the CTA processes
+// nb + 1 raw batches and stores only the outputs of its own range.
+//
+// The FIR uses packed FP32 pairs (fma.rn.f32x2): (re, im) of a sample times
+// its (h, h) tap in one instruction.
+#pragma once
+
+#include "ppf_fwd.cuh"
+
+namespace ppf {
+
+// every FFT stage must give each thread a whole number (>= 1) of items
+constexpr bool fft_items_fit(int C, int B, int NT) {
+    for (int p = 0; p < fft_stages(C); ++p) {
+        const int items = B * (C / fft_radix(C, p));
+        if (items < NT || items % NT != 0) return false;
+    }
+    return true;
+}
+
+template <int C, int TM, int IN>
+struct CarryShape {
+    static constexpr int NT = C / 2;                                 // one channel pair per thread
+    static constexpr int B = 8192 / C;                               // spectra per batch (64 KB of y)
+    static constexpr int BIN = InTraits<IN>::bytes;
+    static constexpr int YBYTES = B * C * 8;
+    static constexpr int SLOTB = B * C * BIN;
+    static constexpr int TWBYTES = tw_size(C) * 8;
+    static constexpr int BASE = YBYTES + 2 * SLOTB + 64;
+    // two CTAs per SM when shared memory allows and the FIR state fits 128 registers
+    static constexpr int MINB = ((BASE + TWBYTES + 1024) * 2 <= 228 * 1024 && TM <= 8) ? 2 : 1;
+    static constexpr int CTA_SMEM_MAX = (MINB == 2 ? 113 * 1024 : 226 * 1024) - 128;
+    static constexpr bool TW_SMEM = BASE + TWBYTES <= CTA_SMEM_MAX;
+    static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
+    static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
+    static constexpr bool OK = (C >= 256 && C <= 1024) && (TM <= 16) && (B >= TM - 1) &&
+                               SMEM <= CTA_SMEM_MAX && fft_items_fit(C, B, NT);
+};
+
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+// d += a * b, two FP32 lanes per instruction
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
+template <int C, int TM, int IN, int OUT>
+__global__ void __launch_bounds__(CarryShape<C, TM, IN>::NT, CarryShape<C, TM, IN>::MINB)
+pfb_fwd_carry_kernel(FwdArgs args) {
+    using S = CarryShape<C, TM, IN>;
+    constexpr int NT = S::NT, B = S::B, BIN = S::BIN;
+    constexpr int NST = fft_stages(C);
+    static_assert(S::OK, "shape not supported by the carry kernel");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* ybuf = reinterpret_cast<float2*>(smem);
+    float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
+    unsigned char* ring = smem + S::RING_OFF;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 2 * S::SLOTB);     // 3 barriers
+    volatile int* sflag = reinterpret_cast<volatile int*>(bars + 3);
+
+    const int tid = threadIdx.x;
+    const int cp = tid;                              // channel pair
+    const long long n_spectra = args.n_spectra;
+    const int T = args.T;
+    const int D = TM - T;                            // leading zero taps of the bucket
+    const long long n_raw = n_spectra + T - 1;
+    const long long nbt = (n_spectra + B - 1) / B;
+    const long long lo = (long long)blockIdx.x * nbt / gridDim.x;
+    const long long hi = (long long)(blockIdx.x + 1) * nbt / gridDim.x;
+    const long long nb = hi - lo;
+    if (nb <= 0) return;
+    const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
+    const long long nraw_b = (T > 1) ? nb + 1 : nb;  // raw batches this CTA streams
+
+    const float2* tws = args.tw;
+    if constexpr (S::TW_SMEM) {
+        for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
+        tws = tw_s;
+    }
+    // taps of this pair, shifted so the bucket's zero taps lead: h'[t] = h[t - D]
+    unsigned long long h0[TM], h1[TM];
+    {
+        const float2* taps2 = reinterpret_cast<const float2*>(args.taps);
+#pragma unroll
+        for (int t = 0; t < TM; ++t) {
+            const float2 h = (t >= D) ? __ldg(taps2 + (t - D) * (C / 2) + cp) : make_float2(0.f, 0.f);
+            h0[t] = pk2(h.x, h.x);
+            h1[t] = pk2(h.y, h.y);
+        }
+    }
+    // carried rows x_i = raw row lo*B - (TM-1) + i, i < TM-1 (zero before the stream)
+    float4 carry[TM > 1 ? TM - 1 : 1];
+#pragma unroll
+    for (int i = 0; i < TM - 1; ++i) {
+        const long long r = lo * B - (TM - 1) + i;
+        carry[i] = (r >= 0 && r < n_raw) ? load_pair_global<IN>(args.in, r * C + 2 * cp)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+
+    auto rows_of = [&](long long j) -> long long {
+        const long long r = n_raw - (lo + j) * B;
+        return r <= 0 ? 0 : (r < B ? r : B);
+    };
+    auto issue = [&](long long j) {
+        const long long rows = rows_of(j);
+        if (rows > 0) {
+            uint64_t* bar = &bars[j & 1];
+            const uint32_t bytes = (uint32_t)(rows * C * BIN);
+            mbar_expect_tx(bar, bytes);
+            tma_load_1d(ring + (j & 1) * S::SLOTB,
+                        static_cast<const unsigned char*>(args.in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
+        }
+    };
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+        *sflag = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        issue(0);
+        if (nraw_b > 1) issue(1);
+    }
+
+    for (long long k = 0; k < nraw_b; ++k) {
+        // ------------------------------------------------ wait for slot k
+        if (tid == 0) {
+            bool ok = rows_of(k) == 0 || mbar_wait_bounded(&bars[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
+            if (k == 0 && (args.flags & FWD_INJECT_TIMEOUT))     // a barrier nothing arrives on
+                ok = ok && mbar_wait_bounded(&bars[2], 0, kInjectedWaitNs);
+            if (!ok) {
+                // give up: let the copies in flight land, then report
+                for (long long j = k; j < k + 2 && j < nraw_b; ++j)
+                    if (rows_of(j) > 0) mbar_wait_bounded(&bars[j & 1], (uint32_t)((j >> 1) & 1), kWaitLimitNs);
+                atomicExch(args.err, 1);
+                *sflag = 1;
+            }
+        }
+        __syncthreads();
+        if (*sflag) return;
+        // ---------------------------------------------------------- FIR
+        // sequence x_i: i < TM-1 carried rows, then the B rows of slot k.
+        // output j = sum_{t < TM} h'[t] x_{j+t}
+        {
+            const unsigned char* slot = ring + (k & 1) * S::SLOTB + 2 * cp * BIN;
+            unsigned long long acc[B][2];
+#pragma unroll
+            for (int j = 0; j < B; ++j) acc[j][0] = acc[j][1] = 0ull;
+            float4 nxt[TM > 1 ? TM - 1 : 1];
+#pragma unroll
+            for (int i = 0; i < B + TM - 1; ++i) {
+                const float4 x = (i < TM - 1) ? carry[i < TM - 1 ? i : 0]
+                                              : load_pair_smem<IN>(slot + (size_t)(i - (TM - 1)) * C * BIN);
+                const unsigned long long x01 = pk2(x.x, x.y), x23 = pk2(x.z, x.w);
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    const int t = i - j;
+                    if (t >= 0 && t < TM) {
+                        if (IN != IN_CF32 || t >= D) {      // fp32: keep inf/NaN out of unrelated outputs
+                            ffma2(acc[j][0], h0[t], x01);
+                            ffma2(acc[j][1], h1[t], x23);
+                        }
+                    }
+                }
+                if (i >= B) nxt[i - B] = x;
+            }
+#pragma unroll
+            for (int i = 0; i < TM - 1; ++i) carry[i] = nxt[i];
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const float2 a = upk2(acc[j][0]), b = upk2(acc[j][1]);
+                *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
+            }
+        }
+        __syncthreads();
+        // slot k is free: refill it with raw batch k+2
+        if (tid == 0 && k + 2 < nraw_b) {
+            fence_proxy_async_smem();
+            issue(k + 2);
+        }
+        // ---------------------------------------------------------- FFT
+        const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
+        static_for<NST>([&](auto p) {
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, vlo, vhi);
+        });
+    }
+}
+
+}  // namespace ppf
