@@ -83,8 +83,36 @@ template <int M, int N> struct Tw {
 };
 
 // ---------------------------------------------------------- complex helpers
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add/sub use the packed FP32 pair instructions of sm_100+ (one
+// instruction for re and im); everything else is scalar FP32.
+__device__ __forceinline__ unsigned long long as_pair(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 from_pair(unsigned long long v) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#ifndef PPF_NO_F32X2
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_pair(a)), "l"(as_pair(b)));
+    return from_pair(r);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#ifndef PPF_NO_F32X2
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(as_pair(a)), "l"(as_pair(b)));
+    return from_pair(r);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
 // a * w for a runtime twiddle w
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
     return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
@@ -130,11 +158,13 @@ __device__ __forceinline__ void r4_bfly(float2 (&v)[N]) {
     constexpr int S = LEN / 4;
     float2 a0 = v[BASE + J], a1 = v[BASE + J + S], a2 = v[BASE + J + 2 * S], a3 = v[BASE + J + 3 * S];
     float2 p = cadd(a0, a2), q = csub(a0, a2);
-    float2 r = cadd(a1, a3), t = cmul_mi(csub(a1, a3));
+    float2 r = cadd(a1, a3), d = csub(a1, a3);
+    // q + (-i) d and q - (-i) d: the swap of d's parts folds into scalar adds
+    const float2 u = make_float2(q.x + d.y, q.y - d.x), w = make_float2(q.x - d.y, q.y + d.x);
     v[BASE + J] = cadd(p, r);
     v[BASE + J + S] = cmul_tw<2 * J, LEN>(csub(p, r));
-    v[BASE + J + 2 * S] = cmul_tw<J, LEN>(cadd(q, t));
-    v[BASE + J + 3 * S] = cmul_tw<3 * J, LEN>(csub(q, t));
+    v[BASE + J + 2 * S] = cmul_tw<J, LEN>(u);
+    v[BASE + J + 3 * S] = cmul_tw<3 * J, LEN>(w);
 }
 
 template <int LEN, int N>

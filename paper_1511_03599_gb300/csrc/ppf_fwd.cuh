@@ -120,7 +120,10 @@ struct FwdArgs {
 
 // One FFT stage over the whole batch held in shared memory.
 // Output spectrum of batch row sp is sb + sp; it is stored when it lies in [vlo, vhi).
-template <int C, int B, int NT, int P, int OUT, bool TW_SMEM>
+// SPW > 0: warp-local mode, warp w owns batch rows [w*SPW, (w+1)*SPW) in every
+// stage, so the stages synchronise with __syncwarp only; SPW == 0: the items
+// of a stage are spread over the whole CTA and __syncthreads separates them.
+template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
@@ -129,25 +132,31 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int NN = NP / R;                 // N_{p+1}
     constexpr int PP = C / NP;                 // prefixes at this stage
     constexpr int ITEMS = C / R;               // items per spectrum
-    constexpr int IPT = B * ITEMS / NT;        // items per thread
-    static_assert(IPT * NT == B * ITEMS, "items must divide evenly");
-    const int tid = threadIdx.x;
+    constexpr int WORKERS = SPW > 0 ? 32 : NT;
+    constexpr int IPT = (SPW > 0 ? SPW : B) * ITEMS / WORKERS;   // items per thread
+    static_assert(IPT * WORKERS == (SPW > 0 ? SPW : B) * ITEMS, "items must divide evenly");
+    const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
+    const int sp0 = SPW > 0 ? (threadIdx.x >> 5) * SPW : 0;
+    auto sync = [] {
+        if constexpr (SPW > 0) __syncwarp();
+        else __syncthreads();
+    };
 
     float2 v[IPT][R];
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
-        const int item = tid + it * NT;
-        const int sp = item / ITEMS, e = item % ITEMS;
+        const int item = wid + it * WORKERS;
+        const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
         const float2* src = ybuf + sp * C;
 #pragma unroll
         for (int a = 0; a < R; ++a) v[it][a] = src[phys<C, P>(prefix * NP + NN * a + b)];
     }
-    __syncthreads();   // every read of this stage is done before anything is overwritten
+    sync();   // every read of this stage is done before anything is overwritten
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
-        const int item = tid + it * NT;
-        const int sp = item / ITEMS, e = item % ITEMS;
+        const int item = wid + it * WORKERS;
+        const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
         dft_reg<R>(v[it]);
         if constexpr (P + 1 < NST) {
@@ -168,7 +177,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             }
         }
     }
-    if constexpr (P + 1 < NST) __syncthreads();
+    if constexpr (P + 1 < NST) sync();
 }
 
 __device__ __forceinline__ void fma_pair(float4& acc, float2 h, float4 x) {

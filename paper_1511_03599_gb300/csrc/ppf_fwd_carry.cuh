@@ -39,13 +39,20 @@ struct CarryShape {
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BASE = YBYTES + 2 * SLOTB + 64;
     // two CTAs per SM when shared memory allows and the FIR state fits 128 registers
+#ifdef PPF_CARRY_ONE_CTA
+    static constexpr int MINB = 1;
+#else
     static constexpr int MINB = ((BASE + TWBYTES + 1024) * 2 <= 228 * 1024 && TM <= 8) ? 2 : 1;
+#endif
     static constexpr int CTA_SMEM_MAX = (MINB == 2 ? 113 * 1024 : 226 * 1024) - 128;
     static constexpr bool TW_SMEM = BASE + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
-    static constexpr bool OK = (C >= 256 && C <= 1024) && (TM <= 16) && (B >= TM - 1) &&
-                               SMEM <= CTA_SMEM_MAX && fft_items_fit(C, B, NT);
+    static constexpr int NWARP = NT >= 32 ? NT / 32 : 1;
+    static constexpr int SPW = B / NWARP;                            // spectra per warp in the FFT
+    static constexpr bool OK = (C >= 256 && C <= 1024) && (NT % 32 == 0) && (TM <= 16) && (B >= TM - 1) &&
+                               SMEM <= CTA_SMEM_MAX && SPW >= 1 && SPW * NWARP == B &&
+                               fft_items_fit(C, SPW, 32);
 };
 
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
@@ -200,7 +207,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
         // ---------------------------------------------------------- FFT
         const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, vlo, vhi);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, args.out, sb, vlo, vhi);
         });
     }
 }
