@@ -100,6 +100,48 @@ ppf_status ppf_execute(ppf_plan_t plan, const void* in_dev, void* out_dev,
                        long long n_spectra, ppf_stream_t stream);
 
 /*
+ * ppf_execute_batched -- ppf_execute over n_streams independent streams (beams)
+ * in one launch.  Stream i reads in_dev + i*in_stride samples and writes
+ * out_dev + i*out_stride samples; strides are in samples (elements of
+ * in_dtype / out_dtype pairs), at least one stream long, and their byte
+ * sizes multiples of 16.  CTAs are spread over the streams; each stream is
+ * transformed exactly as ppf_execute would.  Asynchronous; one launch.
+ * Errors: INVALID_ARG, ALIGNMENT, CUDA.
+ */
+ppf_status ppf_execute_batched(ppf_plan_t plan, const void* in_dev, long long in_stride, void* out_dev,
+                               long long out_stride, long long n_spectra, long long n_streams,
+                               ppf_stream_t stream);
+
+/*
+ * ppf_backward -- adjoint of the transform, for fitting the taps by gradient
+ * descent.  Conjugate-Wirtinger convention (PyTorch's): for a real loss L and
+ * complex z the gradient is dL/dRe(z) + i dL/dIm(z).  With G = grad_out:
+ *   g_y = F^H G (unnormalised inverse DFT, sign +i, per spectrum),
+ *   grad_in[r][c]   = sum_t h[t*C+c] g_y[r-t][c],
+ *   grad_taps[t*C+c] = sum over streams and s of Re(conj(g_y[s][c]) x[s+t][c]).
+ *   grad_out_dev : n_streams * n_spectra*C complex FP32, streams contiguous
+ *   in_dev       : the forward input, n_streams * C*(n_spectra+T-1) complex FP32
+ *   grad_in_dev  : same layout as in_dev (written, not accumulated), or NULL
+ *   grad_taps_dev: C*T floats (written), or NULL; not both NULL
+ * Needs a plan with complex FP32 input, C in [64, 256] and T <= 16 (else
+ * UNSUPPORTED).  The tap gradient is a deterministic two-pass reduction
+ * (per-CTA partial sums, then a fixed-order sum); the partial-sum scratch is
+ * allocated by the plan on the first call and grown when a call needs more
+ * CTAs (cudaMalloc inside the call).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY.
+ */
+ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
+                        float* grad_taps_dev, long long n_spectra, long long n_streams, ppf_stream_t stream);
+
+/*
+ * ppf_update_taps -- replace the plan's C*T coefficients (tap-major, FP32)
+ * with those at taps_dev (device memory), ordered on `stream`: launches
+ * enqueued after it use the new taps.  Used when fitting the taps.
+ * Asynchronous; no allocation.  Errors: INVALID_ARG, CUDA.
+ */
+ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t stream);
+
+/*
  * ppf_execute_host -- the same transform with HOST input and output buffers.
  * The stream is cut into chunks that are copied host->device, transformed
  * and copied device->host on a small pipeline of CUDA streams so that the

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ppf.h"
+#include "ppf_bwd.cuh"
 #include "ppf_fwd.cuh"
 #include "ppf_internal.h"
 
@@ -94,6 +95,11 @@ struct ppf_plan_s {
     int debug_flags;      // testing aid: ppf::FwdFlags passed to the kernel
     ppf::FwdEntry fwd;
     HostPipe* pipe;
+    bool has_bwd;         // adjoint kernel available for this shape
+    ppf::BwdEntry bwd;
+    int bwd_occupancy;
+    float* d_partials;    // tap-gradient partial sums, one row of TM*C per CTA
+    long long partials_ctas;
 };
 
 // Registry of live plans: a handle is checked against it before it is
@@ -175,6 +181,16 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     p->C = C; p->T = T; p->TM = tm; p->device = dev; p->sms = sms; p->occupancy = occ;
     p->grid = sms * occ;
     p->in = in_dtype; p->out = out_dtype; p->fwd = e;
+    if (in_dtype == PPF_IN_CF32 && ppf::bwd_lookup(C, tm, &p->bwd)) {
+        ce = cudaFuncSetAttribute(p->bwd.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->bwd.smem);
+        if (ce == cudaSuccess)
+            ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->bwd_occupancy, p->bwd.fn, p->bwd.threads, p->bwd.smem);
+        if (ce != cudaSuccess) {
+            delete p;
+            return cuda_fail(ce, "ppf_plan: backward kernel attributes");
+        }
+        p->has_bwd = p->bwd_occupancy > 0;
+    }
     register_plan(p);
     ce = cudaMalloc(&p->d_taps, taps.size() * sizeof(float));
     if (ce == cudaSuccess) ce = cudaMalloc(&p->d_tw, tw.size() * sizeof(float));
@@ -191,10 +207,22 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     return PPF_OK;
 }
 
-static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, void* out_dev, long long n, cudaStream_t st) {
+// CTAs per stream: enough to fill the GPU once over all streams, at most one
+// per batch of a stream.
+static int ctas_per_stream(long long target, long long n_streams, long long batches) {
+    long long cps = (target + n_streams - 1) / n_streams;
+    if (cps > batches) cps = batches;
+    if (cps < 1) cps = 1;
+    return (int)cps;
+}
+
+static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, long long in_stride, void* out_dev,
+                             long long out_stride, long long n, long long n_streams, cudaStream_t st) {
     ppf::FwdArgs a;
     a.in = in_dev;
     a.out = out_dev;
+    a.in_stride = in_stride;
+    a.out_stride = out_stride;
     a.taps = p->d_taps;
     a.tw = p->d_tw;
     a.err = p->d_err;
@@ -202,25 +230,99 @@ static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, void* out_dev, lo
     a.T = p->T;
     a.flags = p->debug_flags;
     const long long nb = (n + p->fwd.batch - 1) / p->fwd.batch;
-    const int grid = (int)(nb < p->grid ? nb : p->grid);
-    cudaError_t ce = p->fwd.launch(a, grid, st);
+    a.ctas_per_stream = ctas_per_stream(p->grid, n_streams, nb);
+    const long long grid = (long long)a.ctas_per_stream * n_streams;
+    if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: too many streams");
+    cudaError_t ce = p->fwd.launch(a, (int)grid, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute: launch");
     return PPF_OK;
+}
+
+static bool overlaps(const void* a, unsigned long long na, const void* b, unsigned long long nb) {
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+extern "C" ppf_status ppf_execute_batched(ppf_plan_t p, const void* in_dev, long long in_stride, void* out_dev,
+                                          long long out_stride, long long n_spectra, long long n_streams,
+                                          ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: invalid plan");
+    if (in_dev == nullptr || out_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: NULL buffer");
+    if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: n_spectra=%lld < 1", n_spectra);
+    if (n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: n_streams=%lld < 1", n_streams);
+    const long long in_len = (long long)p->C * (n_spectra + p->T - 1), out_len = (long long)p->C * n_spectra;
+    if (n_streams > 1 && (in_stride < in_len || out_stride < out_len))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_execute: stream strides shorter than one stream");
+    const int bi = bytes_in(p->in), bo = bytes_out(p->out);
+    if ((reinterpret_cast<uintptr_t>(in_dev) & 15) || (reinterpret_cast<uintptr_t>(out_dev) & 15) ||
+        (n_streams > 1 && (((in_stride * bi) & 15) || ((out_stride * bo) & 15))))
+        return fail(PPF_ERR_ALIGNMENT, "ppf_execute: buffers and stream strides must be 16-byte aligned");
+    const unsigned long long in_bytes = (unsigned long long)((n_streams - 1) * in_stride + in_len) * bi;
+    const unsigned long long out_bytes = (unsigned long long)((n_streams - 1) * out_stride + out_len) * bo;
+    if (overlaps(in_dev, in_bytes, out_dev, out_bytes))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_execute: input and output overlap");
+    return launch_fwd(p, in_dev, in_stride, out_dev, out_stride, n_spectra, n_streams,
+                      reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" ppf_status ppf_execute(ppf_plan_t p, const void* in_dev, void* out_dev, long long n_spectra,
                                   ppf_stream_t stream) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: invalid plan");
-    if (in_dev == nullptr || out_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: NULL buffer");
-    if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: n_spectra=%lld < 1", n_spectra);
-    if ((reinterpret_cast<uintptr_t>(in_dev) & 15) || (reinterpret_cast<uintptr_t>(out_dev) & 15))
-        return fail(PPF_ERR_ALIGNMENT, "ppf_execute: buffers must be 16-byte aligned");
-    const unsigned long long in_bytes = (unsigned long long)p->C * (n_spectra + p->T - 1) * bytes_in(p->in);
-    const unsigned long long out_bytes = (unsigned long long)p->C * n_spectra * bytes_out(p->out);
-    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in_dev), o0 = reinterpret_cast<uintptr_t>(out_dev);
-    if (i0 < o0 + out_bytes && o0 < i0 + in_bytes)
-        return fail(PPF_ERR_INVALID_ARG, "ppf_execute: input and output overlap");
-    return launch_fwd(p, in_dev, out_dev, n_spectra, reinterpret_cast<cudaStream_t>(stream));
+    return ppf_execute_batched(p, in_dev, 0, out_dev, 0, n_spectra, 1, stream);
+}
+
+extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
+                                   float* grad_taps_dev, long long n_spectra, long long n_streams,
+                                   ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: invalid plan");
+    if (!p->has_bwd)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward: needs complex FP32 input, C in [64, 256] and T <= 16");
+    if (grad_out_dev == nullptr || in_dev == nullptr || (grad_in_dev == nullptr && grad_taps_dev == nullptr))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_backward: NULL buffer");
+    if (n_spectra < 1 || n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: empty problem");
+    const uintptr_t al = reinterpret_cast<uintptr_t>(grad_out_dev) | reinterpret_cast<uintptr_t>(in_dev) |
+                         reinterpret_cast<uintptr_t>(grad_in_dev) | reinterpret_cast<uintptr_t>(grad_taps_dev);
+    if (al & 15) return fail(PPF_ERR_ALIGNMENT, "ppf_backward: buffers must be 16-byte aligned");
+    const int C = p->C, T = p->T, TM = p->TM;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const long long n_raw = n_spectra + T - 1;
+    const long long in_len = (long long)C * n_raw, out_len = (long long)C * n_spectra;
+    if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), in_dev,
+                                (unsigned long long)(n_streams * in_len * 8)))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps the input");
+    const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
+    const int cps = ctas_per_stream((long long)p->sms * p->bwd_occupancy, n_streams, nb);
+    const long long grid = (long long)cps * n_streams;
+    if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: too many streams");
+    if (grid > p->partials_ctas) {   // scratch for the per-CTA tap-gradient partial sums
+        if (p->d_partials) cudaFree(p->d_partials);
+        p->d_partials = nullptr;
+        p->partials_ctas = 0;
+        cudaError_t ce = cudaMalloc(&p->d_partials, sizeof(float) * (size_t)grid * TM * C);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: partial sums");
+        p->partials_ctas = grid;
+    }
+    ppf::BwdArgs a;
+    a.gY = static_cast<const float2*>(grad_out_dev);
+    a.x = static_cast<const float2*>(in_dev);
+    a.taps = p->d_taps;
+    a.tw = p->d_tw;
+    a.gx = static_cast<float2*>(grad_in_dev);
+    a.partials = p->d_partials;
+    a.err = p->d_err;
+    a.n_spectra = n_spectra;
+    a.gY_stride = out_len;
+    a.x_stride = in_len;
+    a.T = T;
+    a.ctas_per_stream = cps;
+    a.flags = p->debug_flags;
+    cudaError_t ce = p->bwd.launch(a, (int)grid, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: launch");
+    if (grad_taps_dev != nullptr) {
+        ce = ppf::bwd_reduce(p->d_partials, (int)grid, T, TM, C, grad_taps_dev, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: tap-gradient reduction");
+    }
+    return PPF_OK;
 }
 
 static void free_pipe(HostPipe* hp) {
@@ -276,7 +378,7 @@ extern "C" ppf_status ppf_execute_host(ppf_plan_t p, const void* in_host, void* 
         char* dst = static_cast<char*>(out_host) + (size_t)s0 * C * bo;
         ce = cudaMemcpyAsync(hp->d_in[q], src, (size_t)C * (n + T - 1) * bi, cudaMemcpyHostToDevice, hp->st[q]);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: host->device copy");
-        ppf_status s = launch_fwd(p, hp->d_in[q], hp->d_out[q], n, hp->st[q]);
+        ppf_status s = launch_fwd(p, hp->d_in[q], 0, hp->d_out[q], 0, n, 1, hp->st[q]);
         if (s != PPF_OK) return s;
         ce = cudaMemcpyAsync(dst, hp->d_out[q], (size_t)C * n * bo, cudaMemcpyDeviceToHost, hp->st[q]);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: device->host copy");
@@ -296,6 +398,7 @@ extern "C" ppf_status ppf_destroy(ppf_plan_t p) {
     if (p->d_taps) cudaFree(p->d_taps);
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->d_err) cudaFree(p->d_err);
+    if (p->d_partials) cudaFree(p->d_partials);
     p->magic = 0;
     delete p;
     return PPF_OK;
@@ -334,5 +437,14 @@ extern "C" ppf_status ppf_set_debug_flags(ppf_plan_t p, int flags) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: invalid plan");
     if (flags & ~ppf::FWD_INJECT_TIMEOUT) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: unknown flag");
     p->debug_flags = flags;
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_update_taps(ppf_plan_t p, const float* taps_dev, ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_update_taps: invalid plan");
+    if (taps_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_update_taps: NULL taps");
+    cudaError_t ce = cudaMemcpyAsync(p->d_taps, taps_dev, sizeof(float) * (size_t)p->C * p->T,
+                                     cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_update_taps");
     return PPF_OK;
 }

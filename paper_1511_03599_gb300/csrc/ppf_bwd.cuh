@@ -1,0 +1,245 @@
+// ppf_bwd.cuh -- adjoint (backward pass) of the fused PFB for complex FP32
+// input, in the conjugate-Wirtinger convention of PyTorch (for a real loss L
+// and complex z, grad_z = dL/dRe z + i dL/dIm z).
+//
+// The forward map is Y = F y, y[s][c] = sum_t h[t][c] x[s+t][c] (Alg. 1,
+// Eq. 2); it is complex-linear in x and real-linear in h, so with the
+// incoming gradient G = grad_Y:
+//   g_y = F^H G                          (unnormalised inverse DFT, sign +i)
+//   grad_x[r][c] = sum_t h[t][c] g_y[r-t][c]            (transposed FIR)
+//   grad_h[t][c] = sum_r Re(conj(g_y[r-t][c]) x[r][c])  (tap correlation)
+// with g_y[s] = 0 outside 0 <= s < S.  Both sums run over raw rows r, so the
+// work is partitioned by r: each CTA owns a contiguous range of raw rows,
+// needs g_y rows back to r-(T-1) (carried in registers from the previous
+// batch, or from one leading batch it inverse-transforms at its start), and
+// writes every grad_x row of its range exactly once.  The tap gradient is
+// accumulated per thread in registers, written as one partial per CTA, and
+// summed over CTAs in a fixed order by a second kernel (deterministic: no
+// floating-point atomics).
+//
+// Per CTA and batch of B raw rows: TMA copies of the G rows and the x rows
+// of the batch into double-buffered shared-memory slots, the inverse DFT in
+// place in the G slot (warp-local stages), then one thread per channel runs
+// both sums over the batch rows.
+#pragma once
+
+#include "ppf_fwd.cuh"
+
+namespace ppf {
+
+template <int C, int TM>
+struct BwdShape {
+    static constexpr int NT = C;                                     // one channel per thread
+    static constexpr int B = 4096 / C;                               // raw rows per batch
+    static constexpr int SLOTB = B * C * 8;                          // complex FP32 rows of a batch
+    static constexpr int NWARP = NT / 32;
+    static constexpr int SPW = NWARP > 0 ? B / NWARP : 0;            // spectra per warp in the DFT
+    static constexpr int SMEM = 4 * SLOTB + 64;                      // G slots, x slots, barriers
+    static constexpr bool OK = (C >= 64 && C <= 256) && (TM <= 16) && (B >= TM - 1) &&
+                               SPW >= 1 && SPW * NWARP == B && fft_items_fit(C, SPW, 32);
+};
+
+struct BwdArgs {
+    const float2* gY;        // incoming gradient, n_spectra*C per stream
+    const float2* x;         // forward input, C*(n_spectra+T-1) per stream
+    const float* taps;       // TM*C floats, tap-major, rows >= T zero
+    const float2* tw;        // twiddle tables of the forward plan
+    float2* gx;              // grad wrt x, same layout as x (nullptr: skip)
+    float* partials;         // gridDim.x * TM * C tap-gradient partial sums
+    int* err;
+    long long n_spectra;
+    long long gY_stride, x_stride;   // samples between streams
+    int T;
+    int ctas_per_stream;
+    int flags;
+};
+
+template <int C, int TM>
+__global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs args) {
+    using S = BwdShape<C, TM>;
+    constexpr int NT = S::NT, B = S::B, NST = fft_stages(C);
+    static_assert(S::OK, "shape not supported by the backward kernel");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* gslot = reinterpret_cast<float2*>(smem);                    // [2][B][C]
+    float2* xslot = reinterpret_cast<float2*>(smem + 2 * S::SLOTB);     // [2][B][C]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * S::SLOTB);  // g0 g1 x0 x1 never
+    volatile int* sflag = reinterpret_cast<volatile int*>(bars + 5);
+
+    const int c = threadIdx.x;
+    const long long n_spectra = args.n_spectra;
+    const int T = args.T;
+    const long long n_raw = n_spectra + T - 1;
+    const long long nbt = (n_raw + B - 1) / B;        // batches of raw rows
+    const int cps = args.ctas_per_stream;
+    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
+    const float2* gY = args.gY + (size_t)strm * args.gY_stride;
+    const float2* x = args.x + (size_t)strm * args.x_stride;
+    float2* gx = args.gx ? args.gx + (size_t)strm * args.x_stride : nullptr;
+    const long long lo = (long long)bx * nbt / cps;
+    const long long hi = (long long)(bx + 1) * nbt / cps;
+    const long long nb = hi - lo;
+
+    // taps of channel c as (h, h) pairs; tap-gradient accumulators
+    unsigned long long hh[TM], acch[TM];
+#pragma unroll
+    for (int t = 0; t < TM; ++t) {
+        const float h = __ldg(args.taps + t * C + c);
+        hh[t] = pk2(h, h);
+        acch[t] = 0ull;
+    }
+    unsigned long long carry[TM > 1 ? TM - 1 : 1];     // g_y rows (first row) - (TM-1) .. -1
+#pragma unroll
+    for (int i = 0; i < TM - 1; ++i) carry[i] = 0ull;
+
+    // iterations: k = k0 (a leading batch that only fills the carry) .. nb-1
+    const long long k0 = (lo > 0 && TM > 1) ? -1 : 0;
+    const long long nit = nb - k0;
+    auto g_rows = [&](long long j) -> long long {     // valid G rows of absolute batch j
+        const long long r = n_spectra - j * B;
+        return r <= 0 ? 0 : (r < B ? r : B);
+    };
+    auto x_rows = [&](long long j) -> long long {
+        const long long r = n_raw - j * B;
+        return r <= 0 ? 0 : (r < B ? r : B);
+    };
+    auto issue = [&](long long it) {                   // iteration it = k - k0
+        const long long k = it + k0, j = lo + k;
+        const int q = (int)(it & 1);
+        const long long gr = g_rows(j);
+        if (gr > 0) {
+            mbar_expect_tx(&bars[q], (uint32_t)(gr * C * 8));
+            tma_load_1d(gslot + q * B * C, gY + (size_t)j * B * C, (uint32_t)(gr * C * 8), &bars[q]);
+        }
+        const long long xr = k >= 0 ? x_rows(j) : 0;
+        if (xr > 0) {
+            mbar_expect_tx(&bars[2 + q], (uint32_t)(xr * C * 8));
+            tma_load_1d(xslot + q * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + q]);
+        }
+    };
+    auto wait_it = [&](long long it, uint64_t limit) -> bool {
+        const long long k = it + k0, j = lo + k;
+        const uint32_t par = (uint32_t)((it >> 1) & 1);
+        bool ok = true;
+        if (g_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[it & 1], par, limit);
+        if (k >= 0 && x_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[2 + (it & 1)], par, limit);
+        return ok;
+    };
+    if (c == 0) {
+        for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+        *sflag = 0;
+    }
+    __syncthreads();
+    if (nb <= 0) {                                     // no rows: contribute zero partials
+        for (int t = 0; t < TM; ++t) args.partials[(size_t)blockIdx.x * TM * C + t * C + c] = 0.f;
+        return;
+    }
+    if (c == 0) {
+        issue(0);
+        if (nit > 1) issue(1);
+    }
+
+    for (long long it = 0; it < nit; ++it) {
+        const long long k = it + k0, j = lo + k;
+        const int q = (int)(it & 1);
+        float2* gs = gslot + q * B * C;
+        const float2* xs = xslot + q * B * C;
+        if (c == 0) {
+            bool ok = wait_it(it, kWaitLimitNs);
+            if (it == 0 && (args.flags & FWD_INJECT_TIMEOUT)) ok = ok && mbar_wait_bounded(&bars[4], 0, kInjectedWaitNs);
+            if (!ok) {
+                for (long long i2 = it; i2 < it + 2 && i2 < nit; ++i2) wait_it(i2, kWaitLimitNs);
+                atomicExch(args.err, 1);
+                *sflag = 1;
+            }
+        }
+        __syncthreads();
+        if (*sflag) return;
+        // g_y = F^H G for the B rows of the batch, in place (warp-local stages)
+        static_for<NST>([&](auto p) {
+            fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, false, S::SPW, true>(gs, args.tw, nullptr, 0, 0, 0);
+        });
+        __syncthreads();
+        // one thread per channel: sequence g_i = carried rows (i < TM-1) then the batch rows
+        const long long row0 = j * B;                  // first raw row (and G row) of the batch
+        unsigned long long gxa[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) gxa[r] = 0ull;
+        unsigned long long gseq[B + TM - 1];
+#pragma unroll
+        for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
+#pragma unroll
+        for (int r = 0; r < B; ++r) {
+            const float2 g = (row0 + r < n_spectra) ? gs[r * C + c] : make_float2(0.f, 0.f);
+            gseq[TM - 1 + r] = pk2(g.x, g.y);
+        }
+        if (k >= 0) {
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                const float2 xv = (row0 + r < n_raw) ? xs[r * C + c] : make_float2(0.f, 0.f);
+                const unsigned long long xp = pk2(xv.x, xv.y);
+#pragma unroll
+                for (int t = 0; t < TM; ++t) {
+                    if (t < T) {
+                        const unsigned long long g = gseq[TM - 1 + r - t];
+                        ffma2(gxa[r], hh[t], g);        // grad_x[r] += h[t] g_y[r-t]
+                        ffma2(acch[t], g, xp);          // (g.re x.re, g.im x.im)
+                    }
+                }
+            }
+            if (gx != nullptr) {
+#pragma unroll
+                for (int r = 0; r < B; ++r)
+                    if (row0 + r < n_raw) gx[(size_t)(row0 + r) * C + c] = upk2(gxa[r]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TM - 1; ++i) carry[i] = gseq[B + i];
+        __syncthreads();
+        if (c == 0 && it + 2 < nit) {
+            fence_proxy_async_smem();
+            issue(it + 2);
+        }
+    }
+    float* part = args.partials + (size_t)blockIdx.x * TM * C;
+#pragma unroll
+    for (int t = 0; t < TM; ++t) {
+        const float2 a = upk2(acch[t]);
+        part[t * C + c] = a.x + a.y;
+    }
+}
+
+// grad_h[t*C + c] = sum over CTAs, in CTA order, of the partial sums.
+static __global__ void pfb_bwd_reduce_kernel(const float* __restrict__ partials, int nparts, int TC, int TMC,
+                                      float* __restrict__ grad_h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TC) return;
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += partials[(size_t)p * TMC + i];
+    grad_h[i] = s;
+}
+
+struct BwdInfo {
+    int threads, batch, smem;
+    const void* fn;
+};
+
+template <int C, int TM>
+inline BwdInfo bwd_info() {
+    using S = BwdShape<C, TM>;
+    if constexpr (S::OK) return BwdInfo{S::NT, S::B, S::SMEM, reinterpret_cast<const void*>(&pfb_bwd_kernel<C, TM>)};
+    else return BwdInfo{0, 0, 0, nullptr};
+}
+
+template <int C, int TM>
+inline cudaError_t bwd_launch(const BwdArgs& a, int grid, cudaStream_t st) {
+    using S = BwdShape<C, TM>;
+    if constexpr (S::OK) {
+        pfb_bwd_kernel<C, TM><<<grid, S::NT, S::SMEM, st>>>(a);
+        return cudaPeekAtLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace ppf

@@ -108,8 +108,11 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;     // 2 s
 constexpr uint64_t kInjectedWaitNs = 2000000ull;     // 2 ms
 
 struct FwdArgs {
-    const void* in;          // raw stream, C*(n_spectra+T-1) samples
-    void* out;               // n_spectra*C outputs
+    const void* in;          // raw streams, C*(n_spectra+T-1) samples each
+    void* out;               // n_spectra*C outputs per stream
+    long long in_stride;     // samples between consecutive input streams
+    long long out_stride;    // samples between consecutive output streams
+    int ctas_per_stream;     // CTAs that share one stream (grid = streams * this)
     const float* taps;       // TM*C floats, tap-major, rows >= T are zero
     const float2* tw;        // twiddle tables, tw_size(C) entries
     int* err;                // device status word: 1 = a bounded wait gave up
@@ -123,7 +126,10 @@ struct FwdArgs {
 // SPW > 0: warp-local mode, warp w owns batch rows [w*SPW, (w+1)*SPW) in every
 // stage, so the stages synchronise with __syncwarp only; SPW == 0: the items
 // of a stage are spread over the whole CTA and __syncthreads separates them.
-template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0>
+// INV: the unnormalised inverse DFT (sign +i) computed as conj(DFT(conj(.)));
+// its last stage writes the result back into the spectrum's own row of
+// ybuf in natural order instead of to global memory.
+template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
@@ -150,7 +156,10 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         const int b = e % NN, prefix = e / NN;
         const float2* src = ybuf + sp * C;
 #pragma unroll
-        for (int a = 0; a < R; ++a) v[it][a] = src[phys<C, P>(prefix * NP + NN * a + b)];
+        for (int a = 0; a < R; ++a) {
+            v[it][a] = src[phys<C, P>(prefix * NP + NN * a + b)];
+            if constexpr (INV && P == 0) v[it][a].y = -v[it][a].y;
+        }
     }
     sync();   // every read of this stage is done before anything is overwritten
 #pragma unroll
@@ -169,6 +178,10 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             float2* dst = ybuf + sp * C;
 #pragma unroll
             for (int k = 0; k < R; ++k) dst[phys<C, P + 1>((prefix + PP * k) * NN + b)] = v[it][k];
+        } else if constexpr (INV) {
+            float2* dst = ybuf + sp * C;
+#pragma unroll
+            for (int k = 0; k < R; ++k) dst[prefix + PP * k] = make_float2(v[it][k].x, -v[it][k].y);
         } else {
             const long long s = sb + sp;
             if (s >= vlo && s < vhi) {
@@ -177,7 +190,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             }
         }
     }
-    if constexpr (P + 1 < NST) sync();
+    if constexpr (P + 1 < NST || INV) sync();
 }
 
 __device__ __forceinline__ void fma_pair(float4& acc, float2 h, float4 x) {
@@ -290,9 +303,14 @@ pfb_fwd_kernel(FwdArgs args) {
     const int T = args.T;
     const long long n_raw = n_spectra + T - 1;
     const long long nbt = (n_spectra + B - 1) / B;
-    // contiguous range of batches per CTA: raw spectra stream through the CTA once
-    const long long lo = (long long)blockIdx.x * nbt / gridDim.x;
-    const long long hi = (long long)(blockIdx.x + 1) * nbt / gridDim.x;
+    // stream of this CTA and its contiguous range of batches within the stream:
+    // raw spectra stream through the CTA once
+    const int cps = args.ctas_per_stream;
+    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
+    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * S::BIN;
+    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
+    const long long lo = (long long)bx * nbt / cps;
+    const long long hi = (long long)(bx + 1) * nbt / cps;
     const long long nb = hi - lo;
     if (nb <= 0) return;
 
@@ -324,7 +342,7 @@ pfb_fwd_kernel(FwdArgs args) {
             const uint32_t bytes = (uint32_t)(rows * C * S::BIN);
             mbar_expect_tx(bar, bytes);
             tma_load_1d(ring + (j % NS) * S::SLOTB,
-                        static_cast<const unsigned char*>(args.in) + (size_t)(lo + j) * B * C * S::BIN, bytes, bar);
+                        static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * S::BIN, bytes, bar);
         }
     };
     auto wait_upto = [&](long long j) -> bool {            // thread 0: batches < issued only
@@ -370,7 +388,7 @@ pfb_fwd_kernel(FwdArgs args) {
             if (tid == 0 && k + 2 < nb) {           // warm L2 two batches ahead
                 const long long r0 = (sb + 2 * B), rows = (n_raw - r0 < B) ? n_raw - r0 : B;
                 if (rows > 0)
-                    tma_prefetch_l2(static_cast<const unsigned char*>(args.in) + (size_t)r0 * C * S::BIN,
+                    tma_prefetch_l2(static_cast<const unsigned char*>(in) + (size_t)r0 * C * S::BIN,
                                     (uint32_t)(rows * C * S::BIN));
             }
         }
@@ -384,7 +402,7 @@ pfb_fwd_kernel(FwdArgs args) {
                 src.cur = ring + (k % NS) * S::SLOTB + 2 * cp * S::BIN;
                 src.nxt = ring + ((k + 1) % NS) * S::SLOTB + 2 * cp * S::BIN;
             } else {
-                src.in = args.in;
+                src.in = in;
                 src.row0 = sb;
                 src.n_raw = n_raw;
                 src.cp = cp;
@@ -406,7 +424,7 @@ pfb_fwd_kernel(FwdArgs args) {
         }
         // ---------------------------------------------------------- FFT
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, args.out, sb, 0, n_spectra);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, out, sb, 0, n_spectra);
         });
     }
 }

@@ -91,8 +91,12 @@ pfb_fwd_carry_kernel(FwdArgs args) {
     const int D = TM - T;                            // leading zero taps of the bucket
     const long long n_raw = n_spectra + T - 1;
     const long long nbt = (n_spectra + B - 1) / B;
-    const long long lo = (long long)blockIdx.x * nbt / gridDim.x;
-    const long long hi = (long long)(blockIdx.x + 1) * nbt / gridDim.x;
+    const int cps = args.ctas_per_stream;
+    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
+    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
+    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
+    const long long lo = (long long)bx * nbt / cps;
+    const long long hi = (long long)(bx + 1) * nbt / cps;
     const long long nb = hi - lo;
     if (nb <= 0) return;
     const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
@@ -119,7 +123,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
 #pragma unroll
     for (int i = 0; i < TM - 1; ++i) {
         const long long r = lo * B - (TM - 1) + i;
-        carry[i] = (r >= 0 && r < n_raw) ? load_pair_global<IN>(args.in, r * C + 2 * cp)
+        carry[i] = (r >= 0 && r < n_raw) ? load_pair_global<IN>(in, r * C + 2 * cp)
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
@@ -134,7 +138,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
             const uint32_t bytes = (uint32_t)(rows * C * BIN);
             mbar_expect_tx(bar, bytes);
             tma_load_1d(ring + (j & 1) * S::SLOTB,
-                        static_cast<const unsigned char*>(args.in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
+                        static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
         }
     };
     if (tid == 0) {
@@ -207,7 +211,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
         // ---------------------------------------------------------- FFT
         const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, args.out, sb, vlo, vhi);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, out, sb, vlo, vhi);
         });
     }
 }

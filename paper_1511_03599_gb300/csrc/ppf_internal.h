@@ -8,6 +8,7 @@
 namespace ppf {
 
 struct FwdArgs;
+struct BwdArgs;
 
 struct FwdEntry {
     int threads;     // threads per CTA
@@ -19,6 +20,18 @@ struct FwdEntry {
     const void* fn;  // kernel function (for occupancy queries and attributes)
     cudaError_t (*launch)(const FwdArgs&, int grid, cudaStream_t);
 };
+
+struct BwdEntry {
+    int threads;     // threads per CTA
+    int batch;       // raw rows per CTA batch
+    int smem;        // dynamic shared memory bytes
+    const void* fn;
+    cudaError_t (*launch)(const BwdArgs&, int grid, cudaStream_t);
+};
+// Adjoint kernels (complex FP32 input only); false when (C, tap bucket) is not built.
+bool bwd_lookup(int C, int tap_bucket, BwdEntry* e);
+// grad_h[t*C + c] = sum_p partials[p*TM*C + t*C + c], p in order.
+cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, float* grad_h, cudaStream_t st);
 
 // Per-C lookups; return false when the (tap bucket, in, out) triple is not built.
 #define PPF_DECLARE_C(C)                                                         \

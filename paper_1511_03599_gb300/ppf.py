@@ -29,6 +29,10 @@ _SIGS = {
     "ppf_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                 ctypes.c_int, ctypes.c_int]),
     "ppf_execute": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "ppf_execute_batched": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P, ctypes.c_longlong, ctypes.c_longlong,
+                                           ctypes.c_longlong, _P]),
+    "ppf_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
+    "ppf_update_taps": (ctypes.c_int, [_P, _P, _P]),
     "ppf_execute_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
     "ppf_destroy": (ctypes.c_int, [_P]),
     "ppf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -118,17 +122,18 @@ class Plan:
         return dict(zip(keys, list(a)))
 
     def n_spectra_for(self, x) -> int:
-        """Output spectra for an input tensor/array of interleaved samples."""
+        """Output spectra for one stream of interleaved samples (the last dimensions of x)."""
         n_samples = x.numel() if x.is_complex() else x.numel() // 2
         if n_samples % self.C:
             raise ValueError("input length is not a whole number of raw spectra")
         return n_samples // self.C - self.T + 1
 
-    def empty_output(self, n_spectra: int, device=None):
+    def empty_output(self, n_spectra: int, device=None, n_streams: int | None = None):
         import torch
+        lead = () if n_streams is None else (n_streams,)
         if self.out_dtype == "c64":
-            return torch.empty((n_spectra, self.C), dtype=torch.complex64, device=device)
-        return torch.empty((n_spectra, self.C, 2), dtype=torch.float16, device=device)
+            return torch.empty(lead + (n_spectra, self.C), dtype=torch.complex64, device=device)
+        return torch.empty(lead + (n_spectra, self.C, 2), dtype=torch.float16, device=device)
 
     def _check_input(self, x):
         import torch
@@ -139,19 +144,61 @@ class Plan:
         if not x.is_contiguous():
             raise ValueError("input must be contiguous")
 
-    def execute(self, x, out=None, stream=None):
-        """Transform the CUDA tensor ``x``; returns (S, C) complex64 or (S, C, 2) float16."""
+    def execute(self, x, out=None, stream=None, n_streams: int | None = None):
+        """Transform the CUDA tensor ``x``; returns (S, C) complex64 or (S, C, 2) float16.
+
+        With ``n_streams`` the leading dimension of x indexes independent streams
+        (all the same length) and the output gains the same leading dimension.
+        """
         self._check_input(x)
         if not x.is_cuda:
             raise ValueError("execute() needs a CUDA tensor; use execute_host() for host buffers")
-        S = self.n_spectra_for(x)
+        ns = 1 if n_streams is None else int(n_streams)
+        if n_streams is not None and (ns < 1 or x.shape[0] != ns):
+            raise ValueError("the leading dimension of x must equal n_streams")
+        per = x.reshape(ns, -1)[0] if ns > 1 else x
+        S = self.n_spectra_for(per)
         if S < 1:
             raise ValueError(f"input holds fewer than T={self.T} raw spectra")
         if out is None:
-            out = self.empty_output(S, device=x.device)
-        check(lib().ppf_execute(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                S, _stream_handle(stream)))
+            out = self.empty_output(S, device=x.device, n_streams=n_streams)
+        in_stride = self.C * (S + self.T - 1)
+        check(lib().ppf_execute_batched(self.handle, ctypes.c_void_p(x.data_ptr()), in_stride,
+                                        ctypes.c_void_p(out.data_ptr()), S * self.C, S, ns, _stream_handle(stream)))
         return out
+
+    def update_taps(self, taps, stream=None):
+        """Copy C*T FP32 taps (a CUDA tensor) into the plan, ordered on the stream."""
+        import torch
+        t = taps.detach().reshape(-1)
+        if not t.is_cuda or t.dtype != torch.float32 or t.numel() != self.C * self.T:
+            raise TypeError("update_taps() takes C*T float32 CUDA taps")
+        t = t.contiguous()
+        check(lib().ppf_update_taps(self.handle, ctypes.c_void_p(t.data_ptr()), _stream_handle(stream)))
+        self._taps_ref = t   # keep the source alive until the copy has run
+
+    def backward(self, grad_out, x, want_input: bool = True, want_taps: bool = True, stream=None):
+        """Adjoint: (grad wrt x or None, grad wrt taps (C*T float32) or None).
+
+        grad_out: complex64 CUDA tensor (..., S, C); x: the forward input (complex64,
+        or float32 interleaved), with the same leading stream dimension if any.
+        """
+        import torch
+        if self.in_dtype != "cf32":
+            raise TypeError("backward() needs a complex FP32 input plan")
+        if not (grad_out.is_cuda and x.is_cuda) or grad_out.dtype != torch.complex64:
+            raise TypeError("backward() takes complex64 CUDA tensors")
+        grad_out = grad_out.contiguous()
+        x = x.contiguous()
+        S = grad_out.shape[-2]
+        ns = grad_out.numel() // (S * self.C)
+        gx = torch.empty_like(x) if want_input else None
+        gh = torch.empty(self.C * self.T, dtype=torch.float32, device=x.device) if want_taps else None
+        check(lib().ppf_backward(self.handle, ctypes.c_void_p(grad_out.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                 ctypes.c_void_p(gx.data_ptr() if gx is not None else 0),
+                                 ctypes.c_void_p(gh.data_ptr() if gh is not None else 0), S, ns,
+                                 _stream_handle(stream)))
+        return gx, gh
 
     __call__ = execute
 
