@@ -134,6 +134,33 @@ ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* i
                         float* grad_taps_dev, long long n_spectra, long long n_streams, ppf_stream_t stream);
 
 /*
+ * ppf_backward_noalloc -- ppf_backward for callers that cannot allocate device
+ * memory where they run it (a processing loop with a device-memory budget
+ * fixed at start-up, or code where a cudaMalloc -- which may synchronise the
+ * device or fail under memory pressure -- is not allowed).  The paper has no
+ * counterpart; this is a deployment convenience.  Same arguments, results
+ * and errors as ppf_backward, but the per-CTA tap-gradient partial sums live
+ * in one fixed 4 MiB array (1,048,576 floats) inside the library instead of
+ * plan memory, and the call allocates nothing.  The plan itself (made once
+ * at set-up with ppf_plan) still owns the taps and tables.
+ *   - Size limit: each CTA needs a row of tap_bucket*C floats; the call uses
+ *     fewer CTAs when the array is short and returns PPF_ERR_UNSUPPORTED when
+ *     even one CTA per stream does not fit (n_streams * tap_bucket * C >
+ *     1,048,576).
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ *   - Every call on a device shares that device's array, which keeps the last
+ *     call's contents; each call overwrites all the rows it reads, so nothing
+ *     needs clearing.  Calls on one device that overlap on the GPU (for
+ *     instance on two streams) race on the array: order them.
+ *   - Every GPU that loads the library holds the array until process exit.
+ */
+ppf_status ppf_backward_noalloc(ppf_plan_t plan, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
+                                float* grad_taps_dev, long long n_spectra, long long n_streams,
+                                ppf_stream_t stream);
+
+/*
  * ppf_update_taps -- replace the plan's C*T coefficients (tap-major, FP32)
  * with those at taps_dev (device memory), ordered on `stream`: launches
  * enqueued after it use the new taps.  Used when fitting the taps.

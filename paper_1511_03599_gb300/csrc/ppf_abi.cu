@@ -448,3 +448,96 @@ extern "C" ppf_status ppf_update_taps(ppf_plan_t p, const float* taps_dev, ppf_s
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_update_taps");
     return PPF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Backward pass without any allocation.
+//
+// Some callers cannot allocate device memory where they run the PFB: a
+// real-time pipeline stage with a fixed device-memory budget set at start-up,
+// or a loop where a cudaMalloc (which may synchronise the device or fail
+// under memory pressure) is not allowed.  For them the tap-gradient partial
+// sums of ppf_backward live in this fixed file-scope array instead of plan
+// memory.  Every GPU that loads the library holds the array until the process
+// exits.
+// ---------------------------------------------------------------------------
+#define PPF_NOALLOC_PARTIALS_FLOATS (1 << 20)   // 4 MiB of partial sums
+
+static __device__ __align__(256) float g_noalloc_partials[PPF_NOALLOC_PARTIALS_FLOATS];
+
+// Device address of g_noalloc_partials for each device, looked up once with
+// that device current (the host-side name is only a stand-in).
+static std::mutex g_noalloc_mu;
+static std::vector<float*> g_noalloc_ptr;
+
+static ppf_status noalloc_scratch(int dev, float** out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if ((int)g_noalloc_ptr.size() <= dev) g_noalloc_ptr.resize(dev + 1, nullptr);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        int cur = -1;
+        cudaError_t ce = cudaGetDevice(&cur);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: cudaGetDevice");
+        if (cur != dev) return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: the plan's device is not current");
+        float* ptr = nullptr;
+        ce = cudaGetSymbolAddress(reinterpret_cast<void**>(&ptr), g_noalloc_partials);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_dev, const void* in_dev,
+                                           void* grad_in_dev, float* grad_taps_dev, long long n_spectra,
+                                           long long n_streams, ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: invalid plan");
+    if (!p->has_bwd)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward_noalloc: needs complex FP32 input, C in [64, 256] and T <= 16");
+    if (grad_out_dev == nullptr || in_dev == nullptr || (grad_in_dev == nullptr && grad_taps_dev == nullptr))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: NULL buffer");
+    if (n_spectra < 1 || n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: empty problem");
+    const uintptr_t al = reinterpret_cast<uintptr_t>(grad_out_dev) | reinterpret_cast<uintptr_t>(in_dev) |
+                         reinterpret_cast<uintptr_t>(grad_in_dev) | reinterpret_cast<uintptr_t>(grad_taps_dev);
+    if (al & 15) return fail(PPF_ERR_ALIGNMENT, "ppf_backward_noalloc: buffers must be 16-byte aligned");
+    const int C = p->C, T = p->T, TM = p->TM;
+    const long long n_raw = n_spectra + T - 1;
+    const long long in_len = (long long)C * n_raw, out_len = (long long)C * n_spectra;
+    if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), in_dev,
+                                (unsigned long long)(n_streams * in_len * 8)))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: grad_in overlaps the input");
+    // one row of TM*C partial sums per CTA; fewer CTAs per stream if the array is short
+    const long long row = (long long)TM * C;
+    const long long max_ctas = PPF_NOALLOC_PARTIALS_FLOATS / row;
+    if (n_streams > max_ctas)
+        return fail(PPF_ERR_UNSUPPORTED,
+                    "ppf_backward_noalloc: %lld streams need %lld partial sums, more than the fixed %d",
+                    n_streams, n_streams * row, PPF_NOALLOC_PARTIALS_FLOATS);
+    float* partials = nullptr;
+    ppf_status st = noalloc_scratch(p->device, &partials);
+    if (st != PPF_OK) return st;
+    const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
+    int cps = ctas_per_stream((long long)p->sms * p->bwd_occupancy, n_streams, nb);
+    if ((long long)cps * n_streams > max_ctas) cps = (int)(max_ctas / n_streams);
+    const long long grid = (long long)cps * n_streams;
+    ppf::BwdArgs a;
+    a.gY = static_cast<const float2*>(grad_out_dev);
+    a.x = static_cast<const float2*>(in_dev);
+    a.taps = p->d_taps;
+    a.tw = p->d_tw;
+    a.gx = static_cast<float2*>(grad_in_dev);
+    a.partials = partials;    // every CTA overwrites its whole row: nothing needs clearing
+    a.err = p->d_err;
+    a.n_spectra = n_spectra;
+    a.gY_stride = out_len;
+    a.x_stride = in_len;
+    a.T = T;
+    a.ctas_per_stream = cps;
+    a.flags = p->debug_flags;
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t ce = p->bwd.launch(a, (int)grid, cs);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: launch");
+    if (grad_taps_dev != nullptr) {
+        ce = ppf::bwd_reduce(partials, (int)grid, T, TM, C, grad_taps_dev, cs);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: tap-gradient reduction");
+    }
+    return PPF_OK;
+}

@@ -33,6 +33,7 @@ _SIGS = {
                                            ctypes.c_longlong, _P]),
     "ppf_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_update_taps": (ctypes.c_int, [_P, _P, _P]),
+    "ppf_backward_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_execute_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
     "ppf_destroy": (ctypes.c_int, [_P]),
     "ppf_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -1,0 +1,69 @@
+"""ppf_backward_noalloc: the backward pass for callers that cannot allocate.
+
+Some users run the PFB where device allocation is not allowed (a processing
+loop with a device-memory budget fixed at start-up, or code where a cudaMalloc
+could synchronise the device or fail).  ppf_backward_noalloc keeps its
+tap-gradient partial sums in a fixed array inside the library instead of
+allocating them.  These tests call it through the C ABI, twice in a row with
+different shapes, and compare each result with ppf_backward, within the
+adjoint tests' tolerances (relative L2 1e-5 for the input gradient, 1e-4
+for the tap gradient).  The file is named to be collected last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_03599_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1511_03599_gb300 import ppf as m
+    m.lib()
+    return m
+
+
+def _call(ppf, fn, plan, G, x, S, ns):
+    gx = torch.empty_like(x)
+    gh = torch.empty(plan.C * plan.T, dtype=torch.float32, device="cuda")
+    st = getattr(ppf.lib(), fn)(plan.handle, ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                ctypes.c_void_p(gx.data_ptr()), ctypes.c_void_p(gh.data_ptr()), S, ns,
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    ppf.check(st)
+    torch.cuda.synchronize()
+    return gx, gh
+
+
+def test_noalloc_backward_matches_backward_twice(ppf):
+    rng = np.random.default_rng(2024)
+    C, T = 256, 16
+    h = synth.design_taps(C, T)
+    with ppf.Plan(C, T, h, "cf32", "c64") as plan:
+        for S, ns in ((700, 3), (129, 1)):
+            x = torch.from_numpy((rng.standard_normal((ns, C * (S + T - 1)))
+                                  + 1j * rng.standard_normal((ns, C * (S + T - 1)))).astype(np.complex64)).cuda()
+            G = torch.from_numpy((rng.standard_normal((ns, S, C))
+                                  + 1j * rng.standard_normal((ns, S, C))).astype(np.complex64)).cuda()
+            gx_n, gh_n = _call(ppf, "ppf_backward_noalloc", plan, G, x, S, ns)
+            gx_r, gh_r = _call(ppf, "ppf_backward", plan, G, x, S, ns)
+            plan.check_device()
+            assert oracle.rel_l2(gx_n.cpu().numpy(), gx_r.cpu().numpy()) <= 1e-5
+            assert oracle.rel_l2(gh_n.cpu().numpy(), gh_r.cpu().numpy()) <= 1e-4
+
+
+def test_noalloc_rejects_too_many_streams(ppf):
+    C, T = 256, 16
+    with ppf.Plan(C, T, synth.design_taps(C, T), "cf32", "c64") as plan:
+        ns, S = 300, 1          # 300 * 16 * 256 partial sums > the fixed 1,048,576
+        x = torch.zeros(ns, C * (S + T - 1), dtype=torch.complex64, device="cuda")
+        G = torch.zeros(ns, S, C, dtype=torch.complex64, device="cuda")
+        with pytest.raises(ppf.PPFError) as ei:
+            _call(ppf, "ppf_backward_noalloc", plan, G, x, S, ns)
+        assert ei.value.status == 2
