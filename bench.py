@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--spectra", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     return ap.parse_args()
 
@@ -59,17 +60,35 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("ppf_device.cuh", "ppf_fwd.cuh", "ppf_fwd_carry.cuh")
+
+
+def kernel_source_sha():
+    """SHA-256 over the forward kernel's device sources (identifies the profiled code)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1511_03599_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    """DRAM bytes per launch from the committed ncu summary; None unless the
+    summary was taken on the kernel sources as they are now."""
+    vals = {}
     try:
         with open(PROFILE_SUMMARY) as f:
             for line in f:
-                if line.startswith("traffic_bytes_per_launch:"):
-                    v = line.split(":", 1)[1].strip()
-                    return None if v in ("", "null") else float(v)
+                for key in ("traffic_bytes_per_launch:", "kernel_source_sha:"):
+                    if line.startswith(key):
+                        vals[key] = line.split(":", 1)[1].strip()
     except OSError:
-        pass
-    return None
+        return None
+    v = vals.get("traffic_bytes_per_launch:")
+    if v in (None, "", "null") or vals.get("kernel_source_sha:") != kernel_source_sha():
+        return None
+    return float(v)
 
 
 class ClockSampler:
@@ -127,6 +146,62 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_name(w, info):
+    name = "pfb_fwd_carry_kernel" if info["variant"] & 4 else "pfb_fwd_kernel"
+    return f"{name}<{w.C},{info['tap_bucket']},{w.in_dtype},{w.out_dtype}>"
+
+
+def measure_fwd_bwd(steps: int, warmup: int, dev):
+    """Forward vs forward+backward on the differentiable workload: C=256, T=16,
+    64 streams x 8192 spectra of complex64 noise; backward = grad wrt input and
+    taps (inverse DFT, transposed FIR, tap correlation + reduction)."""
+    import torch
+    from paper_1511_03599_gb300 import ppf, synth
+    C, T, S, ns = 256, 16, 8192, 64
+    n_raw = S + T - 1
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_BASE + 5)
+    x = torch.randn((ns, n_raw * C), dtype=torch.complex64, device=dev, generator=g)
+    G = torch.randn((ns, S, C), dtype=torch.complex64, device=dev, generator=g)
+    plan = ppf.Plan(C, T, synth.design_taps(C, T), "cf32", "c64")
+    y = plan.empty_output(S, device=dev, n_streams=ns)
+    gx = torch.empty_like(x)
+    gh = torch.empty(C * T, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def fwd():
+        plan.execute(x, out=y, n_streams=ns, stream=st)
+
+    def fwd_bwd():
+        fwd()
+        ppf.check(ppf.lib().ppf_backward(plan.handle, ppf.ctypes.c_void_p(G.data_ptr()),
+                                         ppf.ctypes.c_void_p(x.data_ptr()), ppf.ctypes.c_void_p(gx.data_ptr()),
+                                         ppf.ctypes.c_void_p(gh.data_ptr()), S, ns,
+                                         ppf.ctypes.c_void_p(st.cuda_stream)))
+
+    def timed(fn):
+        for _ in range(max(3, warmup)):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(steps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    t_f = timed(fwd)
+    t_fb = timed(fwd_bwd)
+    plan.check_device()
+    info = plan.info()
+    plan.close()
+    samples = ns * S * C
+    return {"workload": f"pfb_c{C}_t{T}_{ns}x{S}_cf32_c64", "fwd_ms": t_f, "fwd_bwd_ms": t_fb,
+            "fwd_bwd_over_fwd": t_fb / t_f, "fwd_gsps": samples / t_f / 1e6, "fwd_bwd_gsps": samples / t_fb / 1e6,
+            "fwd_launch": info, "backward": "grad wrt input and taps, tap-gradient two-pass reduction"}
 
 
 def cpu_baseline(w, target_s: float):
@@ -242,6 +317,7 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_step = float(tt.item())
 
+    info = plan.info()
     samples = w.C * w.S
     b_in, b_out = synth.in_bytes_per_sample(w.in_dtype), synth.out_bytes_per_sample(w.out_dtype)
     alg_bytes = w.C * w.n_raw * b_in + w.C * w.S * b_out + 4 * w.C * w.T
@@ -273,11 +349,14 @@ def main():
                "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, 2-stream chunk pipeline"}
         del xh, yh
 
+    fb = None
+    if not args.no_fwd_bwd:
+        fb = measure_fwd_bwd(max(5, args.steps), args.warmup, dev)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cpu = cpu_baseline(w, args.cpu_seconds)
-        info = plan.info()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -288,11 +367,13 @@ def main():
             "hbm_frac": achieved / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "pfb_fwd_kernel<512,8,ci8,c64>", "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": kernel_name(w, info), "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel_ms": kern_s * 1e3},
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
+            "gpu_launches_fwd_bwd": None if fb is None else 3 * max(5, args.steps),
             "e2e": e2e,
+            "fwd_bwd": fb,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
         }

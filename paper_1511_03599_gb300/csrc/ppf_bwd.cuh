@@ -102,6 +102,9 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         const long long r = n_raw - j * B;
         return r <= 0 ? 0 : (r < B ? r : B);
     };
+    // G slots and their barriers are indexed by the iteration it; x slots by the
+    // x batch k (there is no x batch in the leading iteration), so each slot's
+    // n-th use waits for phase n of its own barrier.
     auto issue = [&](long long it) {                   // iteration it = k - k0
         const long long k = it + k0, j = lo + k;
         const int q = (int)(it & 1);
@@ -112,16 +115,17 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         }
         const long long xr = k >= 0 ? x_rows(j) : 0;
         if (xr > 0) {
-            mbar_expect_tx(&bars[2 + q], (uint32_t)(xr * C * 8));
-            tma_load_1d(xslot + q * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + q]);
+            const int qx = (int)(k & 1);
+            mbar_expect_tx(&bars[2 + qx], (uint32_t)(xr * C * 8));
+            tma_load_1d(xslot + qx * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + qx]);
         }
     };
     auto wait_it = [&](long long it, uint64_t limit) -> bool {
         const long long k = it + k0, j = lo + k;
-        const uint32_t par = (uint32_t)((it >> 1) & 1);
         bool ok = true;
-        if (g_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[it & 1], par, limit);
-        if (k >= 0 && x_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[2 + (it & 1)], par, limit);
+        if (g_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[it & 1], (uint32_t)((it >> 1) & 1), limit);
+        if (k >= 0 && x_rows(j) > 0)
+            ok = ok && mbar_wait_bounded(&bars[2 + (k & 1)], (uint32_t)((k >> 1) & 1), limit);
         return ok;
     };
     if (c == 0) {
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         const long long k = it + k0, j = lo + k;
         const int q = (int)(it & 1);
         float2* gs = gslot + q * B * C;
-        const float2* xs = xslot + q * B * C;
+        const float2* xs = xslot + (k & 1) * B * C;
         if (c == 0) {
             bool ok = wait_it(it, kWaitLimitNs);
             if (it == 0 && (args.flags & FWD_INJECT_TIMEOUT)) ok = ok && mbar_wait_bounded(&bars[4], 0, kInjectedWaitNs);

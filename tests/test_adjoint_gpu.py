@@ -31,7 +31,8 @@ def crand(rng, *shape):
 
 
 @pytest.mark.parametrize("C,T,S,ns", [(256, 16, 100, 1), (256, 8, 37, 3), (128, 3, 333, 2), (64, 1, 70, 1),
-                                      (64, 16, 1, 2), (256, 16, 2000, 1)])
+                                      (64, 16, 1, 2), (256, 16, 2000, 1), (256, 16, 8192, 3), (128, 8, 20000, 2),
+                                      (64, 16, 40000, 1)])
 def test_backward_matches_oracle(mods, C, T, S, ns):
     ppf, _ = mods
     rng = np.random.default_rng(C + T + S + ns)
