@@ -327,6 +327,15 @@ def main():
     achieved = alg_bytes / kern_s / 1e9
     traffic = profiled_traffic()
 
+    # achievable DRAM bandwidth for this kernel's read:write mix (context for the roofline)
+    mix = None
+    try:
+        ratio = max(1, round(b_out / b_in))
+        mix = {"read_write_ratio": f"1:{ratio}", "GB_s": ppf.probe_stream(256 << 20, ratio) / 1e9}
+        mix["frac_of_mix"] = achieved / mix["GB_s"]
+    except Exception as e:  # noqa: BLE001 - context only
+        mix = {"error": str(e)}
+
     # end to end through the host-buffer entry point: H2D + kernel + D2H every step
     e2e = None
     if not args.no_e2e:
@@ -368,7 +377,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": kernel_name(w, info), "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel_ms": kern_s * 1e3},
+                         "kernel_ms": kern_s * 1e3, "streaming_mix_peak": mix},
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
             "gpu_launches_fwd_bwd": None if fb is None else 3 * max(5, args.steps),

@@ -232,6 +232,19 @@ ppf_status ppf_set_debug_flags(ppf_plan_t plan, int flags);
  */
 ppf_status ppf_probe_rates(double* rates, int n);
 
+/*
+ * ppf_probe_stream -- achievable DRAM bandwidth for a traffic mix: a streaming
+ * kernel reads in_bytes from in_dev and writes ratio*in_bytes to out_dev
+ * (16-byte vectors, coalesced, streaming hints); *bytes_per_s receives
+ * (1+ratio)*in_bytes / time (best of three timings of three launches,
+ * after a warm-up launch).  The PFB
+ * with int8 input and complex FP32 output moves 1 byte in per 4 out.
+ * Buffers are caller-owned device memory, 16-byte aligned, in_bytes a
+ * multiple of 16, 0 <= ratio <= 16.  Synchronous (legacy default stream).
+ * Errors: INVALID_ARG, CUDA.
+ */
+ppf_status ppf_probe_stream(const void* in_dev, void* out_dev, long long in_bytes, int ratio, double* bytes_per_s);
+
 #ifdef __cplusplus
 }
 #endif

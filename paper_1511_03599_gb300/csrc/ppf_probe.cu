@@ -9,6 +9,7 @@
 // f32x2 FMA counts as two FMAs; a conversion of one value counts as one).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "../../include/ppf.h"
@@ -122,6 +123,22 @@ __global__ void k_cvt_s16(float* out, int iters, uint32_t seed) {
     if (s == 12345.678f) out[blockIdx.x] = s;
 }
 
+// Streaming kernel with a chosen read:write ratio: every thread reads 16-byte
+// vectors from `in` and writes `ratio` 16-byte vectors to `out` (the traffic
+// mix of a PFB with narrow input and wide output, e.g. int8 in, complex FP32
+// out = 1:4).  Grid-stride, coalesced, streaming stores.
+__global__ void k_stream(const uint4* __restrict__ in, uint4* __restrict__ out, long long n_in, int ratio) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += stride) {
+        const uint4 v = __ldcs(in + i);
+        for (int r = 0; r < ratio; ++r) {
+            uint4 w = v;
+            w.x += r;
+            __stcs(out + (size_t)r * n_in + i, w);
+        }
+    }
+}
+
 template <class F>
 double time_kernel(F launch, int reps) {
     cudaEvent_t a, b;
@@ -164,5 +181,28 @@ extern "C" ppf_status ppf_probe_rates(double* rates, int n) {
     cudaFree(out);
     if (e != cudaSuccess) return PPF_ERR_CUDA;
     for (int i = 0; i < n && i < 5; ++i) rates[i] = r[i];
+    return PPF_OK;
+}
+
+// Achievable DRAM bandwidth (bytes read + written per second) of a streaming
+// kernel that reads in_bytes and writes ratio * in_bytes; synchronous, uses
+// caller-provided device buffers (in: in_bytes, out: ratio * in_bytes, both
+// 16-byte aligned, in_bytes a multiple of 16).
+extern "C" ppf_status ppf_probe_stream(const void* in_dev, void* out_dev, long long in_bytes, int ratio,
+                                       double* bytes_per_s) {
+    if (in_dev == nullptr || out_dev == nullptr || bytes_per_s == nullptr || in_bytes < 16 || (in_bytes & 15) ||
+        ratio < 0 || ratio > 16 || ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(out_dev)) & 15))
+        return PPF_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PPF_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PPF_ERR_CUDA;
+    const long long n = in_bytes / 16;
+    double t = 1e30;
+    for (int rep = 0; rep < 3; ++rep)
+        t = fmin(t, time_kernel([&] {
+            k_stream<<<sms * 4, 512>>>(static_cast<const uint4*>(in_dev), static_cast<uint4*>(out_dev), n, ratio);
+        }, 3));
+    if (cudaGetLastError() != cudaSuccess) return PPF_ERR_CUDA;
+    *bytes_per_s = (double)in_bytes * (1 + ratio) / t;
     return PPF_OK;
 }

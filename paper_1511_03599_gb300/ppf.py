@@ -42,6 +42,7 @@ _SIGS = {
     "ppf_check_device": (ctypes.c_int, [_P, _P]),
     "ppf_set_debug_flags": (ctypes.c_int, [_P, ctypes.c_int]),
     "ppf_probe_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    "ppf_probe_stream": (ctypes.c_int, [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -250,3 +251,14 @@ def probe_rates() -> dict:
     check(lib().ppf_probe_rates(r, 5))
     keys = ("ffma", "ffma2", "cvt_s8", "cvt_s8_bias", "cvt_s16")
     return dict(zip(keys, list(r)))
+
+
+def probe_stream(in_bytes: int, ratio: int, device=None) -> float:
+    """Achievable DRAM bytes/s of a read-in_bytes, write-ratio*in_bytes streaming kernel."""
+    import torch
+    a = torch.empty(in_bytes, dtype=torch.uint8, device=device or "cuda")
+    b = torch.empty(max(16, in_bytes * ratio), dtype=torch.uint8, device=device or "cuda")
+    r = ctypes.c_double()
+    check(lib().ppf_probe_stream(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), in_bytes, ratio,
+                                 ctypes.byref(r)))
+    return r.value
