@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     return ap.parse_args()
 
@@ -204,6 +205,35 @@ def measure_fwd_bwd(steps: int, warmup: int, dev):
             "fwd_launch": info, "backward": "grad wrt input and taps, tap-gradient two-pass reduction"}
 
 
+def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
+    """Fused kernel vs the unfused pair (FIR kernel, filtered spectra to HBM,
+    then the DFT kernel) on the benchmark workload (E3 of the paper: the FIR/DFT
+    split of the PPF's time)."""
+    import torch
+    st = torch.cuda.current_stream()
+    yf = torch.empty(y.shape, dtype=torch.complex64, device=dev)
+
+    def timed(fn):
+        for _ in range(max(3, warmup)):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(steps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    t_fused = timed(lambda: plan.execute(x, out=y, stream=st))
+    t_fir = timed(lambda: plan.fir(x, y=yf, stream=st))
+    t_fft = timed(lambda: plan.fft(yf, out=y, stream=st))
+    del yf
+    return {"fused_ms": t_fused, "fir_ms": t_fir, "fft_ms": t_fft, "unfused_ms": t_fir + t_fft,
+            "fusion_speedup": (t_fir + t_fft) / t_fused, "fft_share_unfused": t_fft / (t_fir + t_fft),
+            "note": "unfused = FIR kernel writing complex64 filtered spectra to HBM, then the DFT kernel"}
+
+
 def cpu_baseline(w, target_s: float):
     """The FP64 oracle as it stands, on a bounded sample of the same workload."""
     import numpy as np
@@ -358,6 +388,12 @@ def main():
                "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, 2-stream chunk pipeline"}
         del xh, yh
 
+    abl = None
+    if not args.no_ablation:
+        try:
+            abl = measure_ablation(plan, x, y, max(5, args.steps // 2), args.warmup, dev)
+        except Exception as e:  # noqa: BLE001 - the ablation is context, not the metric
+            abl = {"error": str(e)}
     fb = None
     if not args.no_fwd_bwd:
         fb = measure_fwd_bwd(max(5, args.steps), args.warmup, dev)
@@ -383,6 +419,7 @@ def main():
             "gpu_launches_fwd_bwd": None if fb is None else 3 * max(5, args.steps),
             "e2e": e2e,
             "fwd_bwd": fb,
+            "unfused_ablation": abl,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
         }

@@ -169,6 +169,23 @@ ppf_status ppf_backward_noalloc(ppf_plan_t plan, const void* grad_out_dev, const
 ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t stream);
 
 /*
+ * ppf_fir / ppf_fft -- the unfused form of the same transform, for the
+ * ablation that measures what fusion saves (the paper runs a FIR kernel and
+ * then a batched FFT library call, Sec. 3.2).
+ *   ppf_fir: the FIR alone (Alg. 1): in_dev as for ppf_execute, y_dev
+ *            receives n_spectra*C complex FP32 filtered samples y[s][c].
+ *            Needs C in {256, 512} and T <= 16 (else UNSUPPORTED).
+ *   ppf_fft: the DFT alone (Eq. 2) of n_spectra rows of C complex FP32 values
+ *            at y_dev into out_dev (the plan's output type); runs the fused
+ *            kernel with T = 1 and unit taps (exact); its internal plan is
+ *            made on the first call (allocates a few KB).
+ * ppf_fft(ppf_fir(x)) equals ppf_execute(x) up to FP32 rounding.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA.
+ */
+ppf_status ppf_fir(ppf_plan_t plan, const void* in_dev, void* y_dev, long long n_spectra, ppf_stream_t stream);
+ppf_status ppf_fft(ppf_plan_t plan, const void* y_dev, void* out_dev, long long n_spectra, ppf_stream_t stream);
+
+/*
  * ppf_execute_host -- the same transform with HOST input and output buffers.
  * The stream is cut into chunks that are copied host->device, transformed
  * and copied device->host on a small pipeline of CUDA streams so that the

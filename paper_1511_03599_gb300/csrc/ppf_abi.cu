@@ -59,6 +59,20 @@ bool lookup(int C, int tm, int in, int out, ppf::FwdEntry* e) {
     }
 }
 
+bool lookup_fir(int C, int tm, int in, ppf::FwdEntry* e) {
+    switch (C) {
+        case 32: return ppf::fir_lookup_c32(tm, in, e);
+        case 64: return ppf::fir_lookup_c64(tm, in, e);
+        case 128: return ppf::fir_lookup_c128(tm, in, e);
+        case 256: return ppf::fir_lookup_c256(tm, in, e);
+        case 512: return ppf::fir_lookup_c512(tm, in, e);
+        case 1024: return ppf::fir_lookup_c1024(tm, in, e);
+        case 2048: return ppf::fir_lookup_c2048(tm, in, e);
+        case 4096: return ppf::fir_lookup_c4096(tm, in, e);
+        default: return false;
+    }
+}
+
 bool twiddles(int C, std::vector<float>& pairs) {
     int n = 0;
     switch (C) {
@@ -100,6 +114,10 @@ struct ppf_plan_s {
     int bwd_occupancy;
     float* d_partials;    // tap-gradient partial sums, one row of TM*C per CTA
     long long partials_ctas;
+    bool has_fir;         // FIR-only ablation kernel available for this shape
+    ppf::FwdEntry fir;
+    int fir_grid;
+    ppf_plan_s* fft_sub;  // DFT-only ablation: a T=1, h=1, complex FP32 input plan (made on first use)
 };
 
 // Registry of live plans: a handle is checked against it before it is
@@ -190,6 +208,17 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
             return cuda_fail(ce, "ppf_plan: backward kernel attributes");
         }
         p->has_bwd = p->bwd_occupancy > 0;
+    }
+    if (lookup_fir(C, tm, (int)in_dtype, &p->fir)) {
+        int focc = 0;
+        ce = cudaFuncSetAttribute(p->fir.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->fir.smem);
+        if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&focc, p->fir.fn, p->fir.threads, p->fir.smem);
+        if (ce != cudaSuccess) {
+            delete p;
+            return cuda_fail(ce, "ppf_plan: FIR-only kernel attributes");
+        }
+        p->has_fir = focc > 0;
+        p->fir_grid = sms * focc;
     }
     register_plan(p);
     ce = cudaMalloc(&p->d_taps, taps.size() * sizeof(float));
@@ -394,6 +423,7 @@ extern "C" ppf_status ppf_destroy(ppf_plan_t p) {
     if (p == nullptr) return PPF_OK;
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_destroy: invalid plan");
     unregister_plan(p);
+    if (p->fft_sub) ppf_destroy(p->fft_sub);
     free_pipe(p->pipe);
     if (p->d_taps) cudaFree(p->d_taps);
     if (p->d_tw) cudaFree(p->d_tw);
@@ -540,4 +570,50 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: tap-gradient reduction");
     }
     return PPF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Unfused ablation: the FIR and the DFT as two separate launches with the
+// filtered spectra in global memory between them (the paper's structure).
+// ---------------------------------------------------------------------------
+extern "C" ppf_status ppf_fir(ppf_plan_t p, const void* in_dev, void* y_dev, long long n_spectra,
+                              ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: invalid plan");
+    if (!p->has_fir) return fail(PPF_ERR_UNSUPPORTED, "ppf_fir: needs C in {256, 512} and T <= 16");
+    if (in_dev == nullptr || y_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: NULL buffer");
+    if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: n_spectra=%lld < 1", n_spectra);
+    if ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15)
+        return fail(PPF_ERR_ALIGNMENT, "ppf_fir: buffers must be 16-byte aligned");
+    const unsigned long long in_bytes = (unsigned long long)p->C * (n_spectra + p->T - 1) * bytes_in(p->in);
+    if (overlaps(in_dev, in_bytes, y_dev, (unsigned long long)p->C * n_spectra * 8))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_fir: input and output overlap");
+    ppf::FwdArgs a;
+    a.in = in_dev;
+    a.out = y_dev;
+    a.in_stride = 0;
+    a.out_stride = 0;
+    a.taps = p->d_taps;
+    a.tw = p->d_tw;
+    a.err = p->d_err;
+    a.n_spectra = n_spectra;
+    a.T = p->T;
+    a.flags = p->debug_flags;
+    const long long nb = (n_spectra + p->fir.batch - 1) / p->fir.batch;
+    a.ctas_per_stream = ctas_per_stream(p->fir_grid, 1, nb);
+    cudaError_t ce = p->fir.launch(a, a.ctas_per_stream, reinterpret_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_fir: launch");
+    return PPF_OK;
+}
+
+extern "C" ppf_status ppf_fft(ppf_plan_t p, const void* y_dev, void* out_dev, long long n_spectra,
+                              ppf_stream_t stream) {
+    if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_fft: invalid plan");
+    if (p->fft_sub == nullptr) {
+        std::vector<float> ones((size_t)p->C, 1.0f);
+        ppf_plan_t sub = nullptr;
+        ppf_status st = ppf_plan(&sub, p->C, 1, ones.data(), PPF_IN_CF32, p->out);
+        if (st != PPF_OK) return st;
+        p->fft_sub = sub;
+    }
+    return ppf_execute(p->fft_sub, y_dev, out_dev, n_spectra, stream);
 }

@@ -466,6 +466,30 @@ inline cudaError_t fwd_launch(const FwdArgs& a, int grid, cudaStream_t st) {
     return cudaPeekAtLastError();
 }
 
+// FIR-only ablation kernels (carry shapes only), output complex FP32 rows.
+template <int C, int TM, int IN>
+inline bool fir_info(FwdInfo* i) {
+    if constexpr (CarryShape<C, TM, IN>::OK) {
+        using S = CarryShape<C, TM, IN>;
+        *i = FwdInfo{S::NT, S::B, S::SMEM, 0, TM, 8,
+                     reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT_CF32, true>)};
+        return true;
+    } else {
+        return false;
+    }
+}
+
+template <int C, int TM, int IN>
+inline cudaError_t fir_launch(const FwdArgs& a, int grid, cudaStream_t st) {
+    if constexpr (CarryShape<C, TM, IN>::OK) {
+        using S = CarryShape<C, TM, IN>;
+        pfb_fwd_carry_kernel<C, TM, IN, OUT_CF32, true><<<grid, S::NT, S::SMEM, st>>>(a);
+        return cudaPeekAtLastError();
+    } else {
+        return cudaErrorNotSupported;
+    }
+}
+
 // Twiddle table contents (host, FP64 -> FP32): stage p < P-1 holds
 // W_{N_p}^{b k} = exp(-2 pi i b k / N_p) at [tw_offset(p) + k*N_{p+1} + b].
 template <int C>

@@ -70,7 +70,10 @@ __device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long 
     asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
 }
 
-template <int C, int TM, int IN, int OUT>
+// FIRONLY: the unfused ablation -- the FIR alone, writing the filtered
+// spectra y (complex FP32, spectrum-major) to global memory instead of
+// transforming them (the paper's FIR kernel followed by a separate DFT).
+template <int C, int TM, int IN, int OUT, bool FIRONLY = false>
 __global__ void __launch_bounds__(CarryShape<C, TM, IN>::NT, CarryShape<C, TM, IN>::MINB)
 pfb_fwd_carry_kernel(FwdArgs args) {
     using S = CarryShape<C, TM, IN>;
@@ -196,10 +199,23 @@ pfb_fwd_carry_kernel(FwdArgs args) {
             }
 #pragma unroll
             for (int i = 0; i < TM - 1; ++i) carry[i] = nxt[i];
+            if constexpr (FIRONLY) {
+                const long long sb = (lo + k) * B - (T - 1);
 #pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const float2 a = upk2(acc[j][0]), b = upk2(acc[j][1]);
-                *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
+                for (int j = 0; j < B; ++j) {
+                    const long long s = sb + j;
+                    if (s >= vlo && s < vhi) {
+                        const float2 a = upk2(acc[j][0]), b = upk2(acc[j][1]);
+                        __stcs(reinterpret_cast<float4*>(static_cast<float2*>(out) + s * C + 2 * cp),
+                               make_float4(a.x, a.y, b.x, b.y));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < B; ++j) {
+                    const float2 a = upk2(acc[j][0]), b = upk2(acc[j][1]);
+                    *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
+                }
             }
         }
         __syncthreads();
@@ -209,10 +225,12 @@ pfb_fwd_carry_kernel(FwdArgs args) {
             issue(k + 2);
         }
         // ---------------------------------------------------------- FFT
-        const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
-        static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, out, sb, vlo, vhi);
-        });
+        if constexpr (!FIRONLY) {
+            const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
+            static_for<NST>([&](auto p) {
+                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, out, sb, vlo, vhi);
+            });
+        }
     }
 }
 

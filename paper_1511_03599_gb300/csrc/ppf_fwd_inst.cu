@@ -51,6 +51,35 @@ bool PPF_CAT(fwd_lookup_c, PPF_C)(int tm, int in, int out, FwdEntry* e) {
     }
 }
 
+template <int TM, int IN>
+static bool make_fir(FwdEntry* e) {
+    FwdInfo i;
+    if (!fir_info<PPF_C, TM, IN>(&i)) return false;
+    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fir_launch<PPF_C, TM, IN>};
+    return true;
+}
+
+template <int TM>
+static bool fir_by_in(int in, FwdEntry* e) {
+    switch (in) {
+        case IN_CI8: return make_fir<TM, IN_CI8>(e);
+        case IN_CI16: return make_fir<TM, IN_CI16>(e);
+        case IN_CF32: return make_fir<TM, IN_CF32>(e);
+        default: return false;
+    }
+}
+
+bool PPF_CAT(fir_lookup_c, PPF_C)(int tm, int in, FwdEntry* e) {
+    switch (tm) {
+        case 1: return fir_by_in<1>(in, e);
+        case 2: return fir_by_in<2>(in, e);
+        case 4: return fir_by_in<4>(in, e);
+        case 8: return fir_by_in<8>(in, e);
+        case 16: return fir_by_in<16>(in, e);
+        default: return false;
+    }
+}
+
 int PPF_CAT(fwd_twiddle_count_c, PPF_C)() { return tw_size(PPF_C) > 0 ? tw_size(PPF_C) : 1; }
 
 void PPF_CAT(fwd_twiddles_c, PPF_C)(float* host_pairs) {

@@ -36,6 +36,7 @@ cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, 
 // Per-C lookups; return false when the (tap bucket, in, out) triple is not built.
 #define PPF_DECLARE_C(C)                                                         \
     bool fwd_lookup_c##C(int tap_bucket, int in, int out, FwdEntry* e);         \
+    bool fir_lookup_c##C(int tap_bucket, int in, FwdEntry* e);                  \
     int fwd_twiddle_count_c##C();                                                \
     void fwd_twiddles_c##C(float* host_pairs);
 PPF_DECLARE_C(32)

@@ -33,6 +33,8 @@ _SIGS = {
                                            ctypes.c_longlong, _P]),
     "ppf_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_update_taps": (ctypes.c_int, [_P, _P, _P]),
+    "ppf_fir": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "ppf_fft": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
     "ppf_backward_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_execute_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
     "ppf_destroy": (ctypes.c_int, [_P]),
@@ -167,6 +169,26 @@ class Plan:
         in_stride = self.C * (S + self.T - 1)
         check(lib().ppf_execute_batched(self.handle, ctypes.c_void_p(x.data_ptr()), in_stride,
                                         ctypes.c_void_p(out.data_ptr()), S * self.C, S, ns, _stream_handle(stream)))
+        return out
+
+    def fir(self, x, y=None, stream=None):
+        """FIR alone (unfused ablation): (S, C) complex64 filtered spectra."""
+        import torch
+        self._check_input(x)
+        S = self.n_spectra_for(x)
+        if y is None:
+            y = torch.empty((S, self.C), dtype=torch.complex64, device=x.device)
+        check(lib().ppf_fir(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), S,
+                            _stream_handle(stream)))
+        return y
+
+    def fft(self, y, out=None, stream=None):
+        """DFT alone (unfused ablation) of (S, C) complex64 rows."""
+        S = y.numel() // self.C
+        if out is None:
+            out = self.empty_output(S, device=y.device)
+        check(lib().ppf_fft(self.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()), S,
+                            _stream_handle(stream)))
         return out
 
     def update_taps(self, taps, stream=None):
