@@ -63,6 +63,7 @@ typedef enum {
 } ppf_status;
 
 typedef struct ppf_plan_s* ppf_plan_t;
+typedef struct ppf_beams_s* ppf_beams_t;
 typedef void* ppf_stream_t;     /* cudaStream_t */
 
 /* Largest supported values. */
@@ -167,6 +168,42 @@ ppf_status ppf_backward_noalloc(ppf_plan_t plan, const void* grad_out_dev, const
  * Asynchronous; no allocation.  Errors: INVALID_ARG, CUDA.
  */
 ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t stream);
+
+/*
+ * Multi-beam channelisation in one persistent launch (many independent beams
+ * with uneven C, T and spectrum counts, e.g. the sub-bands of a receiver).
+ *
+ * ppf_beams_plan -- n_beams beams; beam i has C[i] channels (a power of two
+ *   in [64, 4096]), T[i] <= 16 taps, n_spectra[i] output spectra and taps_host[i]
+ *   (C[i]*T[i] FP32, tap-major; read during the call).  Complex int8 input and
+ *   complex FP32 output only (else UNSUPPORTED).  The plan cuts every beam
+ *   into tiles of about 2^20 samples, sorts them largest first and keeps taps,
+ *   twiddles, descriptors, tiles, a work-queue counter and a status word in
+ *   device memory it allocates.  Synchronous.
+ * ppf_beams_bind -- the device buffers of every beam (in_dev[i]: C[i]*(n_spectra[i]
+ *   +T[i]-1) samples, out_dev[i]: n_spectra[i]*C[i] outputs; 16-byte aligned);
+ *   copied to the device descriptors (synchronous).  Rebind when they change.
+ * ppf_beams_set_tiling -- re-cut the tiles to about tile_samples samples each
+ *   (the autotuner's knob); synchronous.
+ * ppf_beams_execute -- enqueue one queue-counter reset and ONE launch of the
+ *   persistent kernel (ctas_per_sm CTAs per SM, clamped to what fits; 0 =
+ *   most that fit).  Each CTA pulls tiles from the counter and runs the
+ *   beam's FIR + DFT for the tile; every beam's result equals ppf_execute's.
+ *   Asynchronous on `stream`; no allocation.
+ * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=max CTAs
+ *   per SM, [4]=SMs, [5]=dynamic shared memory bytes.
+ * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
+ * ppf_beams_destroy -- free everything (NULL accepted).
+ * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY, DEVICE_TIMEOUT.
+ */
+ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C, const int* T, const long long* n_spectra,
+                          const float* const* taps_host, ppf_in_t in_dtype, ppf_out_t out_dtype);
+ppf_status ppf_beams_bind(ppf_beams_t beams, const void* const* in_dev, void* const* out_dev);
+ppf_status ppf_beams_set_tiling(ppf_beams_t beams, long long tile_samples);
+ppf_status ppf_beams_execute(ppf_beams_t beams, int ctas_per_sm, ppf_stream_t stream);
+ppf_status ppf_beams_info(ppf_beams_t beams, long long info[6]);
+ppf_status ppf_beams_check_device(ppf_beams_t beams, ppf_stream_t stream);
+ppf_status ppf_beams_destroy(ppf_beams_t beams);
 
 /*
  * ppf_fir / ppf_fft -- the unfused form of the same transform, for the

@@ -28,6 +28,18 @@ ppf_status fail(ppf_status s, const char* fmt, ...) {
     return s;
 }
 
+}  // namespace
+
+ppf_status ppf::set_error(ppf_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+namespace {
+
 ppf_status cuda_fail(cudaError_t e, const char* what) {
     if (e == cudaErrorMemoryAllocation)
         return fail(PPF_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));

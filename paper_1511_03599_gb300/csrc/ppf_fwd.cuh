@@ -75,9 +75,9 @@ constexpr int tw_offset(int C, int p) {
 constexpr int tw_size(int C) { return tw_offset(C, fft_stages(C) - 1); }
 
 // ------------------------------------------------------------ launch shape
-template <int C, int TM, int IN>
+template <int C, int TM, int IN, int NTO = 0>
 struct FwdShape {
-    static constexpr int NT = C >= 2048 ? 512 : 256;                 // threads per CTA
+    static constexpr int NT = NTO ? NTO : (C >= 2048 ? 512 : 256);   // threads per CTA
     static constexpr int PAIRS = C / 2;
     static constexpr int B = (C >= 4096) ? 2 : (C >= 2048) ? 4 : 8192 / C;   // spectra per batch
     static constexpr int L0 = TM >= 32 ? 8 : 16;
@@ -284,14 +284,17 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
     }
 }
 
-template <int C, int TM, int IN, int OUT>
-__global__ void __launch_bounds__(FwdShape<C, TM, IN>::NT, FwdShape<C, TM, IN>::NT == 256 ? 2 : 1)
-pfb_fwd_kernel(FwdArgs args) {
-    using S = FwdShape<C, TM, IN>;
+// The FIR + DFT of output batches [lo, hi) of one stream (in/out already
+// offset to the stream), by the whole CTA, using `smem`.  Returns false when
+// a bounded wait gave up (the status word is then set).  Safe to call again
+// for another range (the tile loop of the multi-beam kernel).
+template <int C, int TM, int IN, int OUT, int NTO = 0>
+__device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, void* out, long long lo,
+                                          long long hi, unsigned char* smem) {
+    using S = FwdShape<C, TM, IN, NTO>;
     constexpr int NT = S::NT, B = S::B, L = S::L, NS = S::NS;
     constexpr int NST = fft_stages(C);
     constexpr bool RING = S::RING;
-    extern __shared__ __align__(128) unsigned char smem[];
     float2* ybuf = reinterpret_cast<float2*>(smem);
     float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
     unsigned char* ring = smem + S::RING_OFF;
@@ -302,18 +305,9 @@ pfb_fwd_kernel(FwdArgs args) {
     const long long n_spectra = args.n_spectra;
     const int T = args.T;
     const long long n_raw = n_spectra + T - 1;
-    const long long nbt = (n_spectra + B - 1) / B;
-    // stream of this CTA and its contiguous range of batches within the stream:
-    // raw spectra stream through the CTA once
-    const int cps = args.ctas_per_stream;
-    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
-    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * S::BIN;
-    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
-    const long long lo = (long long)bx * nbt / cps;
-    const long long hi = (long long)(bx + 1) * nbt / cps;
     const long long nb = hi - lo;
-    if (nb <= 0) return;
-
+    if (nb <= 0) return true;
+    __syncthreads();   // the previous range of this CTA is done with shared memory
     const float2* tws = args.tw;
     if constexpr (S::TW_SMEM) {
         for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
@@ -383,7 +377,7 @@ pfb_fwd_kernel(FwdArgs args) {
                 }
             }
             __syncthreads();
-            if (*sflag) return;
+            if (*sflag) return false;
         } else {
             if (tid == 0 && k + 2 < nb) {           // warm L2 two batches ahead
                 const long long r0 = (sb + 2 * B), rows = (n_raw - r0 < B) ? n_raw - r0 : B;
@@ -427,6 +421,24 @@ pfb_fwd_kernel(FwdArgs args) {
             fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, out, sb, 0, n_spectra);
         });
     }
+    return true;
+}
+
+template <int C, int TM, int IN, int OUT>
+__global__ void __launch_bounds__(FwdShape<C, TM, IN>::NT, FwdShape<C, TM, IN>::NT == 256 ? 2 : 1)
+pfb_fwd_kernel(FwdArgs args) {
+    using S = FwdShape<C, TM, IN>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // stream of this CTA and its contiguous range of batches within the stream:
+    // raw spectra stream through the CTA once
+    const long long nbt = (args.n_spectra + S::B - 1) / S::B;
+    const int cps = args.ctas_per_stream;
+    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
+    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * S::BIN;
+    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
+    const long long lo = (long long)bx * nbt / cps;
+    const long long hi = (long long)(bx + 1) * nbt / cps;
+    fwd_range<C, TM, IN, OUT>(args, in, out, lo, hi, smem);
 }
 
 // Host side: shape + launch of one instantiation.

@@ -5,7 +5,13 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/ppf.h"
+
 namespace ppf {
+
+// Record the detail of an error for ppf_last_error_message (calling thread)
+// and return the status.
+ppf_status set_error(ppf_status s, const char* fmt, ...);
 
 struct FwdArgs;
 struct BwdArgs;

@@ -34,6 +34,15 @@ _SIGS = {
     "ppf_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_update_taps": (ctypes.c_int, [_P, _P, _P]),
     "ppf_fir": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
+    "ppf_beams_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_float)), ctypes.c_int, ctypes.c_int]),
+    "ppf_beams_bind": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "ppf_beams_set_tiling": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "ppf_beams_execute": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "ppf_beams_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "ppf_beams_check_device": (ctypes.c_int, [_P, _P]),
+    "ppf_beams_destroy": (ctypes.c_int, [_P]),
     "ppf_fft": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
     "ppf_backward_noalloc": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P]),
     "ppf_execute_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_longlong, _P]),
