@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-beams", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     return ap.parse_args()
 
@@ -234,6 +235,49 @@ def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
             "note": "unfused = FIR kernel writing complex64 filtered spectra to HBM, then the DFT kernel"}
 
 
+def measure_beams(steps: int, dev, seed: int = 4):
+    """The multi-beam workload: 96 beams, C in {64..4096}, T in {4, 8, 16},
+    spectra per beam uniform in [2^12, 2^17], complex int8 sigma=16 in, complex
+    FP32 out, one persistent launch replayed from a CUDA graph after autotuning."""
+    import numpy as np
+    import torch
+    from paper_1511_03599_gb300 import beams, synth
+    rng = np.random.default_rng(synth.SEED_BASE + seed)
+    n = 96
+    C = [int(c) for c in rng.choice([64, 128, 256, 512, 1024, 2048, 4096], n)]
+    T = [int(t) for t in rng.choice([4, 8, 16], n)]
+    S = [int(s) for s in rng.integers(1 << 12, (1 << 17) + 1, n)]
+    taps = [synth.design_taps(c, t) for c, t in zip(C, T)]
+    bs = beams.BeamSet(C, T, S, taps)
+    ins = [synth.stream_torch(c, s + t - 1, "ci8", 16.0, synth.SEED_BASE + seed + 17 * i, (), device=dev)
+           for i, (c, t, s) in enumerate(zip(C, T, S))]
+    outs = [torch.empty((s, c), dtype=torch.complex64, device=dev) for c, s in zip(C, S)]
+    bs.bind(ins, outs)
+    tune = beams.autotune(bs, cache_path=None)
+    g = bs.capture_graph()
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        g.replay()
+    b.record(st)
+    torch.cuda.synchronize()
+    bs.check_device()
+    ms = a.elapsed_time(b) / steps
+    peak, kind = measured_peaks()
+    gbs = bs.bytes_moved() / ms / 1e6
+    res = {"workload": f"{n} beams, C in 64..4096, T in 4/8/16, S in [2^12, 2^17], ci8->c64",
+           "samples": bs.samples(), "ms": ms, "gsps": bs.samples() / ms / 1e6, "GB_s": gbs,
+           "hbm_frac": gbs / peak, "tile_samples": tune["tile_samples"], "ctas_per_sm": tune["ctas_per_sm"],
+           "launches_per_step": 1, "graph": True, "tiles": bs.info()["tiles"]}
+    bs.close()
+    del ins, outs
+    return res
+
+
 def cpu_baseline(w, target_s: float):
     """The FP64 oracle as it stands, on a bounded sample of the same workload."""
     import numpy as np
@@ -394,6 +438,12 @@ def main():
             abl = measure_ablation(plan, x, y, max(5, args.steps // 2), args.warmup, dev)
         except Exception as e:  # noqa: BLE001 - the ablation is context, not the metric
             abl = {"error": str(e)}
+    bm = None
+    if not args.no_beams:
+        try:
+            bm = measure_beams(max(5, args.steps // 2), dev)
+        except Exception as e:  # noqa: BLE001 - reported beside the metric
+            bm = {"error": str(e)}
     fb = None
     if not args.no_fwd_bwd:
         fb = measure_fwd_bwd(max(5, args.steps), args.warmup, dev)
@@ -420,6 +470,7 @@ def main():
             "e2e": e2e,
             "fwd_bwd": fb,
             "unfused_ablation": abl,
+            "batched_beams": bm,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
         }

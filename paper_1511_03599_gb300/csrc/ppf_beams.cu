@@ -85,7 +85,7 @@ __device__ __forceinline__ bool beam_dispatch(int cls, const BeamsArgs& a, const
     else return true;
 }
 
-__global__ void __launch_bounds__(kBeamThreads, 1) pfb_beams_kernel(BeamsArgs a) {
+__global__ void __launch_bounds__(kBeamThreads, 2) pfb_beams_kernel(BeamsArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ unsigned long long s_tile;
     for (;;) {
