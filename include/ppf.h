@@ -55,7 +55,7 @@ typedef enum {
 typedef enum {
     PPF_OK = 0,
     PPF_ERR_INVALID_ARG = 1,     /* null pointer, C<1, T<1, n_spectra<1, overlap, bad handle */
-    PPF_ERR_UNSUPPORTED = 2,     /* C not a power of two in [32, 4096], T > 64, unknown dtype */
+    PPF_ERR_UNSUPPORTED = 2,     /* C not supported (see ppf_plan), T > 64, unknown dtype */
     PPF_ERR_ALIGNMENT = 3,       /* a buffer is not 16-byte aligned */
     PPF_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed */
     PPF_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait gave up (see ppf_device_status) */
@@ -75,8 +75,11 @@ typedef void* ppf_stream_t;     /* cudaStream_t */
  * ppf_plan -- validate (C, T, types), copy the C*T FP32 coefficients to
  * device memory owned by the plan and pick the kernel for the shapes.
  *   out        : receives the plan handle (set to NULL on failure)
- *   C          : channels per spectrum, a power of two in [32, 4096] (Sec. 2;
- *                the paper needs C divisible by 32, Sec. 4.1)
+ *   C          : channels per spectrum: a power of two in [32, 4096], or
+ *                3*2^k in {384, 768, 1536, 3072} (mixed-radix DFT with a
+ *                radix-3 stage; the paper's non-power-of-two example is
+ *                C = 3072, Sec. 4.2 / 5.3).  The paper needs C divisible by 32
+ *                (Sec. 4.1).
  *   T          : taps, 1 <= T <= 64
  *   coeffs_host: C*T host floats, tap-major: coeffs_host[t*C + c] is tap t of
  *                channel c (coefficients are unique per channel and tap and

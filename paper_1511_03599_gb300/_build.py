@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUTDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libppf.so")
-CHANNELS = (32, 64, 128, 256, 512, 1024, 2048, 4096)
+CHANNELS = (32, 64, 128, 256, 512, 1024, 2048, 4096, 384, 768, 1536, 3072)
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -67,6 +67,10 @@ bool lookup(int C, int tm, int in, int out, ppf::FwdEntry* e) {
         case 1024: return ppf::fwd_lookup_c1024(tm, in, out, e);
         case 2048: return ppf::fwd_lookup_c2048(tm, in, out, e);
         case 4096: return ppf::fwd_lookup_c4096(tm, in, out, e);
+        case 384: return ppf::fwd_lookup_c384(tm, in, out, e);
+        case 768: return ppf::fwd_lookup_c768(tm, in, out, e);
+        case 1536: return ppf::fwd_lookup_c1536(tm, in, out, e);
+        case 3072: return ppf::fwd_lookup_c3072(tm, in, out, e);
         default: return false;
     }
 }
@@ -81,6 +85,10 @@ bool lookup_fir(int C, int tm, int in, ppf::FwdEntry* e) {
         case 1024: return ppf::fir_lookup_c1024(tm, in, e);
         case 2048: return ppf::fir_lookup_c2048(tm, in, e);
         case 4096: return ppf::fir_lookup_c4096(tm, in, e);
+        case 384: return ppf::fir_lookup_c384(tm, in, e);
+        case 768: return ppf::fir_lookup_c768(tm, in, e);
+        case 1536: return ppf::fir_lookup_c1536(tm, in, e);
+        case 3072: return ppf::fir_lookup_c3072(tm, in, e);
         default: return false;
     }
 }
@@ -90,6 +98,7 @@ bool twiddles(int C, std::vector<float>& pairs) {
     switch (C) {
 #define PPF_TW(CC) case CC: n = ppf::fwd_twiddle_count_c##CC(); pairs.assign(2 * n, 0.f); ppf::fwd_twiddles_c##CC(pairs.data()); return true;
         PPF_TW(32) PPF_TW(64) PPF_TW(128) PPF_TW(256) PPF_TW(512) PPF_TW(1024) PPF_TW(2048) PPF_TW(4096)
+        PPF_TW(384) PPF_TW(768) PPF_TW(1536) PPF_TW(3072)
 #undef PPF_TW
         default: return false;
     }
@@ -172,9 +181,10 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     *out = nullptr;
     if (coeffs_host == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_plan: coefficients are NULL");
     if (C < 1 || T < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_plan: C=%d, T=%d must be >= 1", C, T);
-    if ((C & (C - 1)) != 0 || C < PPF_MIN_CHANNELS || C > PPF_MAX_CHANNELS)
-        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: C=%d is not a power of two in [%d, %d]", C,
-                    PPF_MIN_CHANNELS, PPF_MAX_CHANNELS);
+    const bool c3 = (C == 384 || C == 768 || C == 1536 || C == 3072);
+    if (!c3 && ((C & (C - 1)) != 0 || C < PPF_MIN_CHANNELS || C > PPF_MAX_CHANNELS))
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: C=%d is neither a power of two in [%d, %d] nor 3*2^k in [384, 3072]",
+                    C, PPF_MIN_CHANNELS, PPF_MAX_CHANNELS);
     if (T > PPF_MAX_TAPS) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: T=%d > %d", T, PPF_MAX_TAPS);
     if (in_dtype < PPF_IN_CI8 || in_dtype > PPF_IN_CF32)
         return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: unknown input type %d", (int)in_dtype);

@@ -185,10 +185,21 @@ __device__ __forceinline__ void dif_stage(float2 (&v)[N]) {
 }
 
 // dft_reg<N>: v[k] <- sum_n v[n] exp(-2 pi i n k / N), natural order in/out.
+// N a power of two, or 3 (first stage of the C = 3 * 2^k transforms).
 template <int N>
 __device__ __forceinline__ void dft_reg(float2 (&v)[N]) {
-    static_assert(is_pow2(N), "radix must be a power of two");
-    if constexpr (N > 1) {
+    static_assert(is_pow2(N) || N == 3, "radix must be a power of two or 3");
+    if constexpr (N == 3) {
+        // W = exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+        constexpr float h = 0.866025403784438646763723170752936183f;   // sqrt(3)/2
+        const float2 s = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
+        const float2 d = make_float2(v[1].x - v[2].x, v[1].y - v[2].y);
+        const float2 t = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+        const float2 u = make_float2(h * d.y, -h * d.x);                  // -i sqrt(3)/2 d
+        v[0] = make_float2(v[0].x + s.x, v[0].y + s.y);
+        v[1] = make_float2(t.x + u.x, t.y + u.y);
+        v[2] = make_float2(t.x - u.x, t.y - u.y);
+    } else if constexpr (N > 1) {
         dif_stage<N>(v);
         float2 t[N];
         static_for<N>([&](auto k) { t[decltype(k)::value] = v[bitrev(decltype(k)::value, ilog2(N))]; });

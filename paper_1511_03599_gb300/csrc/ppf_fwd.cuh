@@ -30,9 +30,16 @@
 namespace ppf {
 
 // -------------------------------------------------------------- FFT plan
-constexpr int fft_stages(int C) { return C >= 2048 ? 3 : 2; }
+// C = 2^k: two stages up to 1024, three above.  C = 3 * 2^k: a radix-3
+// stage first, then two power-of-two stages.
+constexpr bool is_c3(int C) { return C == 384 || C == 768 || C == 1536 || C == 3072; }
+constexpr int fft_stages(int C) { return (C >= 2048 || is_c3(C)) ? 3 : 2; }
 constexpr int fft_radix(int C, int p) {
     switch (C) {
+        case 384:  return p == 0 ? 3 : p == 1 ? 8 : 16;
+        case 768:  return p == 0 ? 3 : 16;
+        case 1536: return p == 0 ? 3 : p == 1 ? 32 : 16;
+        case 3072: return p == 0 ? 3 : 32;
         case 32:   return p == 0 ? 8 : 4;
         case 64:   return 8;
         case 128:  return p == 0 ? 16 : 8;
@@ -79,12 +86,14 @@ template <int C, int TM, int IN, int NTO = 0>
 struct FwdShape {
     static constexpr int NT = NTO ? NTO : (C >= 2048 ? 512 : 256);   // threads per CTA
     static constexpr int PAIRS = C / 2;
-    static constexpr int B = (C >= 4096) ? 2 : (C >= 2048) ? 4 : 8192 / C;   // spectra per batch
+    // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k)
+    static constexpr int B = (C >= 4096) ? 2 : (C >= 2048) ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
     static constexpr int L0 = TM >= 32 ? 8 : 16;
     static constexpr int L = L0 < B ? L0 : B;                        // FIR segment (outputs)
     static constexpr int G = B / L;                                  // segments per batch
     static constexpr int FIR_ITEMS = PAIRS * G;                      // (pair, segment) items
-    static constexpr int FPT = FIR_ITEMS / NT;                       // FIR items per thread
+    static constexpr int FPT = (FIR_ITEMS + NT - 1) / NT;           // FIR items per thread
+    static constexpr bool FIR_EXACT = FIR_ITEMS % NT == 0;
     static constexpr int YBYTES = B * C * 8;                         // filtered spectra of a batch
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BIN = InTraits<IN>::bytes;
@@ -99,7 +108,7 @@ struct FwdShape {
     static constexpr int SMEM = RING_OFF + (RING ? NS * SLOTB + 64 : 0);
     // each thread keeps one channel pair for the whole run: taps stay in registers
     static constexpr bool TAPS_IN_REGS = (FPT == 1) && (TM <= 16) && (NT % PAIRS == 0);
-    static_assert(FPT * NT == FIR_ITEMS && FPT >= 1, "FIR items must divide evenly");
+    static_assert(FPT >= 1 && (FIR_EXACT || is_c3(C)), "FIR items must divide evenly");
     static_assert(SLOTB % 16 == 0 && YBYTES % 16 == 0 && TWBYTES % 16 == 0, "16-byte alignment");
 };
 
@@ -139,8 +148,10 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int PP = C / NP;                 // prefixes at this stage
     constexpr int ITEMS = C / R;               // items per spectrum
     constexpr int WORKERS = SPW > 0 ? 32 : NT;
-    constexpr int IPT = (SPW > 0 ? SPW : B) * ITEMS / WORKERS;   // items per thread
-    static_assert(IPT * WORKERS == (SPW > 0 ? SPW : B) * ITEMS, "items must divide evenly");
+    constexpr int TOTAL = (SPW > 0 ? SPW : B) * ITEMS;
+    constexpr int IPT = (TOTAL + WORKERS - 1) / WORKERS;        // items per thread
+    constexpr bool EXACT = IPT * WORKERS == TOTAL;
+    static_assert(EXACT || (SPW == 0 && is_c3(C)), "items must divide evenly");
     const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
     const int sp0 = SPW > 0 ? (threadIdx.x >> 5) * SPW : 0;
     auto sync = [] {
@@ -152,6 +163,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
         const int item = wid + it * WORKERS;
+        if (!EXACT && item >= TOTAL) break;
         const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
         const float2* src = ybuf + sp * C;
@@ -165,6 +177,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
         const int item = wid + it * WORKERS;
+        if (!EXACT && item >= TOTAL) break;
         const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
         dft_reg<R>(v[it]);
@@ -390,6 +403,7 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
 #pragma unroll 1
         for (int f = 0; f < S::FPT; ++f) {
             const int item = tid + f * NT;
+            if (!S::FIR_EXACT && item >= S::FIR_ITEMS) break;
             const int cp = item % S::PAIRS, g = item / S::PAIRS;
             RawSrc<C, IN, RING, B> src;
             if constexpr (RING) {

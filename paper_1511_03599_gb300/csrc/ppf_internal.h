@@ -53,6 +53,10 @@ PPF_DECLARE_C(512)
 PPF_DECLARE_C(1024)
 PPF_DECLARE_C(2048)
 PPF_DECLARE_C(4096)
+PPF_DECLARE_C(384)
+PPF_DECLARE_C(768)
+PPF_DECLARE_C(1536)
+PPF_DECLARE_C(3072)
 #undef PPF_DECLARE_C
 
 }  // namespace ppf

@@ -59,7 +59,8 @@ def _plan(L, C, T, taps, i=0, o=0, out=True):
 
 @pytest.mark.parametrize("C,T,i,o,want", [
     (0, 8, 0, 0, 1), (512, 0, 0, 0, 1), (-4, 8, 0, 0, 1),
-    (48, 8, 0, 0, 2), (8192, 8, 0, 0, 2), (16, 8, 0, 0, 2), (512, 65, 0, 0, 2),
+    (48, 8, 0, 0, 2), (8192, 8, 0, 0, 2), (16, 8, 0, 0, 2), (512, 65, 0, 0, 2), (96, 8, 0, 0, 2),
+    (6144, 8, 0, 0, 2), (640, 8, 0, 0, 2),
     (512, 8, 3, 0, 2), (512, 8, 0, 2, 2), (512, 8, -1, 0, 2),
 ])
 def test_plan_rejects_bad_arguments(L, C, T, i, o, want):

@@ -64,6 +64,16 @@ def test_parity_channels_taps_ci8(ppf, C, T):
     run_case(ppf, C, T, S, "ci8", "c64", seed=1000 + C + T)
 
 
+# C = 3 * 2^k: a radix-3 DFT stage, then power-of-two stages (the paper's
+# non-power-of-two example is C = 3072)
+@pytest.mark.parametrize("C", [384, 768, 1536, 3072])
+@pytest.mark.parametrize("T,in_dtype,out_dtype", [(1, "cf32", "c64"), (8, "ci8", "c64"), (16, "ci16", "c16"),
+                                                  (5, "cf32", "c64"), (64, "ci8", "c64")])
+def test_parity_non_power_of_two_channels(ppf, C, T, in_dtype, out_dtype):
+    S = max(3, 12288 // C) + 3
+    run_case(ppf, C, T, S, in_dtype, out_dtype, seed=4000 + C + T)
+
+
 @pytest.mark.parametrize("in_dtype", ["ci8", "ci16", "cf32"])
 @pytest.mark.parametrize("out_dtype", ["c64", "c16"])
 @pytest.mark.parametrize("T", [2, 4, 8, 16, 32, 64])
