@@ -211,3 +211,26 @@ def stream_torch(C: int, n_raw: int, in_dtype: str, sigma: float, seed: int, ton
             lim = _IN_LIMIT[in_dtype]
             out[lo:hi] = torch.clamp(torch.round(z), -lim, lim).to(tdt)
     return out
+
+
+def tone_set(C: int, n_raw: int, n_streams: int, seed: int, device="cuda"):
+    """One tone per stream for fitting taps: stream i carries
+    exp(+2 pi i (k_i + d_i) n / C), k_i a channel, d_i in +-{0.1, 0.2, 0.3, 0.45}
+    (between bin centres, where leakage and scalloping are largest, Sec. 2).
+    Returns (x complex64 of shape (n_streams, n_raw*C), k, d)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = rng.integers(0, C, n_streams)
+    d = rng.choice([-0.45, -0.3, -0.2, -0.1, 0.1, 0.2, 0.3, 0.45], n_streams)
+    n = torch.arange(n_raw * C, device=device, dtype=torch.float64)
+    xs = []
+    for ki, di in zip(k, d):
+        ph = torch.remainder(n * (float(ki) + float(di)) / C, 1.0) * (2 * math.pi)
+        xs.append(torch.polar(torch.ones_like(ph), ph).to(torch.complex64))
+    return torch.stack(xs), k, d
+
+
+def noisy_taps(C: int, T: int, noise: float, seed: int) -> np.ndarray:
+    """sinc-Hamming taps plus seeded Gaussian noise of the given standard deviation (FP32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (design_taps(C, T).astype(np.float64) + noise * rng.standard_normal(C * T)).astype(np.float32)
