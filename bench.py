@@ -346,9 +346,8 @@ def main():
     import torch.distributed as dist
     from paper_1511_03599_gb300 import ppf
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1511_03599_gb300 import dist as pdist
+    rank, local, world = pdist.env_rank_world()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -356,12 +355,10 @@ def main():
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = pdist.barrier
 
     # each rank processes its own stream shard of the same shape (weak scaling)
-    x = synth.stream_torch(w.C, w.n_raw, w.in_dtype, w.sigma, w.seed + 7919 * rank, w.tones, device=dev)
+    x = synth.stream_torch(w.C, w.n_raw, w.in_dtype, w.sigma, pdist.rank_seed(w.seed, rank), w.tones, device=dev)
     h = w.taps()
     plan = ppf.Plan(w.C, w.T, h, w.in_dtype, w.out_dtype)
     y = plan.empty_output(w.S, device=dev)
@@ -385,11 +382,7 @@ def main():
     barrier()
     per_launch_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
-    t_step = total_ms / 1e3 / args.steps
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = pdist.max_over_ranks(total_ms / 1e3 / args.steps, device=dev)
 
     info = plan.info()
     samples = w.C * w.S
@@ -421,11 +414,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             plan.execute_host(xh, out=yh)
-        te = (time.perf_counter() - t0) / n_e2e
-        if world > 1:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
+        te = pdist.max_over_ranks((time.perf_counter() - t0) / n_e2e, device=dev)
         e2e = {"value": world * samples / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
