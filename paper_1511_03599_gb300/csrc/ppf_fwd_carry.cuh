@@ -32,19 +32,24 @@ constexpr bool fft_items_fit(int C, int B, int NT) {
 template <int C, int TM, int IN>
 struct CarryShape {
     static constexpr int NT = C / 2;                                 // one channel pair per thread
-    static constexpr int B = 8192 / C;                               // spectra per batch (64 KB of y)
+    // spectra per batch: 64 KB of filtered spectra for C >= 512, 32 KB below
+    // (smaller CTAs, so more of them fit on an SM)
+    static constexpr int B = (C <= 256 ? 4096 : 8192) / C;
     static constexpr int BIN = InTraits<IN>::bytes;
     static constexpr int YBYTES = B * C * 8;
     static constexpr int SLOTB = B * C * BIN;
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BASE = YBYTES + 2 * SLOTB + 64;
-    // two CTAs per SM when shared memory allows and the FIR state fits 128 registers
-#ifdef PPF_CARRY_ONE_CTA
-    static constexpr int MINB = 1;
-#else
-    static constexpr int MINB = ((BASE + TWBYTES + 1024) * 2 <= 228 * 1024 && TM <= 8) ? 2 : 1;
-#endif
-    static constexpr int CTA_SMEM_MAX = (MINB == 2 ? 113 * 1024 : 226 * 1024) - 128;
+    // CTAs per SM: limited by shared memory and by the registers the FIR
+    // state needs (<= 128 per thread up to 8 taps, up to 255 above)
+    static constexpr int SMEM_PER_SM = 228 * 1024;
+    static constexpr int REGS = TM <= 8 ? 128 : 255;
+    static constexpr int CTAS_REG = 65536 / (NT * REGS);
+    static constexpr int CTAS_SMEM = SMEM_PER_SM / (BASE + TWBYTES + 1024);
+    static constexpr int MINB_RAW = CTAS_REG < CTAS_SMEM ? CTAS_REG : CTAS_SMEM;
+    static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 4 ? 4 : MINB_RAW);
+    static constexpr int CTA_SMEM_CAP = SMEM_PER_SM / MINB - 1024 - 128;
+    static constexpr int CTA_SMEM_MAX = CTA_SMEM_CAP < 226 * 1024 ? CTA_SMEM_CAP : 226 * 1024;
     static constexpr bool TW_SMEM = BASE + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
