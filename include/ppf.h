@@ -214,7 +214,9 @@ ppf_status ppf_beams_destroy(ppf_beams_t beams);
  * then a batched FFT library call, Sec. 3.2).
  *   ppf_fir: the FIR alone (Alg. 1): in_dev as for ppf_execute, y_dev
  *            receives n_spectra*C complex FP32 filtered samples y[s][c].
- *            Needs C in {256, 512} and T <= 16 (else UNSUPPORTED).
+ *            Exists where the fused kernel carries its halo in registers:
+ *            C in {64, 128, 256, 512} (and 1024 for int8 input), T <= 16
+ *            (else UNSUPPORTED).
  *   ppf_fft: the DFT alone (Eq. 2) of n_spectra rows of C complex FP32 values
  *            at y_dev into out_dev (the plan's output type); runs the fused
  *            kernel with T = 1 and unit taps (exact); its internal plan is

@@ -601,7 +601,8 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
 extern "C" ppf_status ppf_fir(ppf_plan_t p, const void* in_dev, void* y_dev, long long n_spectra,
                               ppf_stream_t stream) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: invalid plan");
-    if (!p->has_fir) return fail(PPF_ERR_UNSUPPORTED, "ppf_fir: needs C in {256, 512} and T <= 16");
+    if (!p->has_fir)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_fir: needs C in {64, 128, 256, 512} (1024 for int8) and T <= 16");
     if (in_dev == nullptr || y_dev == nullptr) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: NULL buffer");
     if (n_spectra < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_fir: n_spectra=%lld < 1", n_spectra);
     if ((reinterpret_cast<uintptr_t>(in_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15)

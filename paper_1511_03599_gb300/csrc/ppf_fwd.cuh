@@ -151,7 +151,8 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int TOTAL = (SPW > 0 ? SPW : B) * ITEMS;
     constexpr int IPT = (TOTAL + WORKERS - 1) / WORKERS;        // items per thread
     constexpr bool EXACT = IPT * WORKERS == TOTAL;
-    static_assert(EXACT || (SPW == 0 && is_c3(C)), "items must divide evenly");
+    static_assert(EXACT || (SPW == 0 && is_c3(C)) || (SPW > 0 && TOTAL < WORKERS),
+                  "items must divide evenly (a warp may leave lanes idle)");
     const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
     const int sp0 = SPW > 0 ? (threadIdx.x >> 5) * SPW : 0;
     auto sync = [] {

@@ -16,6 +16,8 @@
 // its (h, h) tap in one instruction.
 #pragma once
 
+#include <type_traits>
+
 #include "ppf_fwd.cuh"
 
 namespace ppf {
@@ -28,26 +30,41 @@ constexpr bool fft_items_fit(int C, int B, int NT) {
     }
     return true;
 }
+// warp-local stages with SPW spectra per warp: every stage either fills the
+// warp with whole items per lane or leaves lanes idle (fewer than 32 items),
+// and no lane holds more than 64 floats of data
+constexpr bool warp_fft_ok(int C, int SPW) {
+    for (int p = 0; p < fft_stages(C); ++p) {
+        const int R = fft_radix(C, p);
+        const int items = SPW * (C / R);
+        if (items >= 32 && items % 32 != 0) return false;
+        const int ipt = (items + 31) / 32;
+        if (ipt * R * 2 > 64) return false;
+    }
+    return true;
+}
 
-template <int C, int TM, int IN>
-struct CarryShape {
+// Launch shape of the carry kernel for a batch of B spectra.
+template <int C, int TM, int IN, int B_>
+struct CarryCand {
     static constexpr int NT = C / 2;                                 // one channel pair per thread
-    // spectra per batch: 64 KB of filtered spectra for C >= 512, 32 KB below
-    // (smaller CTAs, so more of them fit on an SM)
-    static constexpr int B = (C <= 256 ? 4096 : 8192) / C;
+    static constexpr int B = B_;
     static constexpr int BIN = InTraits<IN>::bytes;
     static constexpr int YBYTES = B * C * 8;
     static constexpr int SLOTB = B * C * BIN;
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BASE = YBYTES + 2 * SLOTB + 64;
-    // CTAs per SM: limited by shared memory and by the registers the FIR
-    // state needs (<= 128 per thread up to 8 taps, up to 255 above)
+    // registers of the FIR state (accumulators, carried rows, (h, h) taps)
+    static constexpr int REGS_EST = 4 * B + 4 * (TM - 1) + 4 * TM + 4;
+    static constexpr int REGS = REGS_EST <= 64 ? 64 : REGS_EST <= 80 ? 80 : REGS_EST <= 96 ? 96
+                              : REGS_EST <= 128 ? 128 : REGS_EST <= 168 ? 168 : 255;
     static constexpr int SMEM_PER_SM = 228 * 1024;
-    static constexpr int REGS = TM <= 8 ? 128 : 255;
     static constexpr int CTAS_REG = 65536 / (NT * REGS);
     static constexpr int CTAS_SMEM = SMEM_PER_SM / (BASE + TWBYTES + 1024);
-    static constexpr int MINB_RAW = CTAS_REG < CTAS_SMEM ? CTAS_REG : CTAS_SMEM;
-    static constexpr int MINB = MINB_RAW < 1 ? 1 : (MINB_RAW > 4 ? 4 : MINB_RAW);
+    static constexpr int CTAS_THR = 2048 / NT < 32 ? 2048 / NT : 32;
+    static constexpr int M1 = CTAS_REG < CTAS_SMEM ? CTAS_REG : CTAS_SMEM;
+    static constexpr int M2 = M1 < CTAS_THR ? M1 : CTAS_THR;
+    static constexpr int MINB = M2 < 1 ? 1 : M2;                     // CTAs per SM
     static constexpr int CTA_SMEM_CAP = SMEM_PER_SM / MINB - 1024 - 128;
     static constexpr int CTA_SMEM_MAX = CTA_SMEM_CAP < 226 * 1024 ? CTA_SMEM_CAP : 226 * 1024;
     static constexpr bool TW_SMEM = BASE + TWBYTES <= CTA_SMEM_MAX;
@@ -55,10 +72,32 @@ struct CarryShape {
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
     static constexpr int NWARP = NT >= 32 ? NT / 32 : 1;
     static constexpr int SPW = B / NWARP;                            // spectra per warp in the FFT
-    static constexpr bool OK = (C >= 256 && C <= 1024) && (NT % 32 == 0) && (TM <= 16) && (B >= TM - 1) &&
-                               SMEM <= CTA_SMEM_MAX && SPW >= 1 && SPW * NWARP == B &&
-                               fft_items_fit(C, SPW, 32);
+    static constexpr bool OK = (C >= 64 && C <= 1024) && (NT % 32 == 0) && (TM <= 16) && (B >= TM - 1) &&
+                               SMEM <= CTA_SMEM_MAX && SPW >= 1 && SPW * NWARP == B && warp_fft_ok(C, SPW);
+    static constexpr int SCORE = OK ? MINB * NT : 0;                 // resident threads per SM
 };
+
+template <class A, class X>
+struct better_cand {
+    using type = typename std::conditional<(X::SCORE > A::SCORE), X, A>::type;
+};
+
+// The carry kernel's shape.  Batches of 16 spectra are kept for C >= 512
+// and for fp32 input at C = 256, where they already allow two CTAs per SM
+// (smaller batches there measured slower: at C = 512 they spill, at C = 256
+// fp32 the per-batch overhead costs more than the extra CTAs give).  Otherwise batch
+// sizes 16, 8 and 4 are tried and the one with the most resident threads per
+// SM wins (the larger batch on ties).
+template <int C, int TM, int IN>
+struct CarryShapeSel {
+    using C16 = CarryCand<C, TM, IN, 16>;
+    using Best = typename better_cand<typename better_cand<C16, CarryCand<C, TM, IN, 8>>::type,
+                                      CarryCand<C, TM, IN, 4>>::type;
+    static constexpr bool KEEP16 = C16::OK && (C >= 512 || (C == 256 && IN == IN_CF32 && C16::MINB >= 2));
+    using type = typename std::conditional<KEEP16, C16, Best>::type;
+};
+template <int C, int TM, int IN>
+struct CarryShape : CarryShapeSel<C, TM, IN>::type {};
 
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
     unsigned long long r;

@@ -19,7 +19,8 @@ def ppf():
 
 
 @pytest.mark.parametrize("C,T,S,dt", [(512, 8, 333, "ci8"), (512, 16, 40, "ci16"), (256, 16, 1000, "cf32"),
-                                      (256, 3, 17, "ci8"), (512, 1, 5, "cf32")])
+                                      (256, 3, 17, "ci8"), (512, 1, 5, "cf32"), (64, 8, 900, "ci16"),
+                                      (128, 16, 300, "cf32"), (1024, 8, 77, "ci8")])
 def test_fir_only_matches_oracle(ppf, C, T, S, dt):
     h = synth.design_taps(C, T)
     x = synth.stream(C, S + T - 1, dt, {"ci8": 16.0, "ci16": 2000.0, "cf32": 1.0}[dt], 10 + T)
@@ -51,7 +52,7 @@ def test_fft_only_matches_oracle(ppf, C, out_dtype):
 
 
 def test_fir_only_unsupported_shape(ppf):
-    with ppf.Plan(1024, 8, synth.design_taps(1024, 8), "ci8", "c64") as plan:
+    with ppf.Plan(2048, 8, synth.design_taps(2048, 8), "ci8", "c64") as plan:
         with pytest.raises(ppf.PPFError) as ei:
-            plan.fir(torch.zeros(1024 * 20 * 2, dtype=torch.int8, device="cuda"))
+            plan.fir(torch.zeros(2048 * 20 * 2, dtype=torch.int8, device="cuda"))
         assert ei.value.status == 2
