@@ -204,10 +204,32 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: SM count");
     ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: shared memory attribute");
-    int occ = 0;
-    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, e.smem);
-    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: occupancy");
-    if (occ < 1) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: kernel does not fit on an SM");
+    int occ = 0, grid_ctas = 0;
+    if (e.cluster > 0) {
+        // persistent grid: as many whole clusters as can be resident at once
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = e.cluster;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3(e.cluster * sms, 1, 1);
+        cfg.blockDim = dim3(e.threads, 1, 1);
+        cfg.dynamicSmemBytes = e.smem;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        ce = cudaOccupancyMaxActiveClusters(&clusters, e.fn, &cfg);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: cluster occupancy");
+        if (clusters < 1) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: a cluster of the kernel does not fit");
+        occ = 1;
+        grid_ctas = clusters * e.cluster;
+    } else {
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, e.smem);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: occupancy");
+        if (occ < 1) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: kernel does not fit on an SM");
+        grid_ctas = sms * occ;
+    }
 
     // Device tables: taps padded to the bucket with zero rows, twiddles.
     std::vector<float> taps((size_t)tm * C, 0.f);
@@ -219,7 +241,7 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     if (p == nullptr) return fail(PPF_ERR_OUT_OF_MEMORY, "ppf_plan: host allocation");
     p->magic = kMagic;
     p->C = C; p->T = T; p->TM = tm; p->device = dev; p->sms = sms; p->occupancy = occ;
-    p->grid = sms * occ;
+    p->grid = grid_ctas;
     p->in = in_dtype; p->out = out_dtype; p->fwd = e;
     if (in_dtype == PPF_IN_CF32 && ppf::bwd_lookup(C, tm, &p->bwd)) {
         ce = cudaFuncSetAttribute(p->bwd.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->bwd.smem);
@@ -281,8 +303,9 @@ static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, long long in_stri
     a.T = p->T;
     a.flags = p->debug_flags;
     const long long nb = (n + p->fwd.batch - 1) / p->fwd.batch;
-    a.ctas_per_stream = ctas_per_stream(p->grid, n_streams, nb);
-    const long long grid = (long long)a.ctas_per_stream * n_streams;
+    const int unit = p->fwd.cluster > 0 ? p->fwd.cluster : 1;      // CTAs per work unit
+    a.ctas_per_stream = ctas_per_stream(p->grid / unit, n_streams, nb);
+    const long long grid = (long long)a.ctas_per_stream * n_streams * unit;
     if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: too many streams");
     cudaError_t ce = p->fwd.launch(a, (int)grid, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute: launch");

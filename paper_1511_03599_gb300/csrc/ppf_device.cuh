@@ -314,6 +314,47 @@ __device__ __forceinline__ void tma_prefetch_l2(const void* src_gmem, uint32_t b
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
 }
 
+// Bulk copy shared -> global through the async proxy (bulk-group completion).
+// dst, src and bytes must be multiples of 16.  The writing threads make their
+// shared-memory stores visible to the async proxy (fence_proxy_async_smem)
+// and synchronise before one thread issues the copy.
+__device__ __forceinline__ void tma_store_1d(void* dst_gmem, const void* src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// The source shared memory of every committed bulk store may be overwritten.
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Every committed bulk store has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// One complex sample (2 floats) at byte address p of shared memory / global memory.
+template <int IN>
+__device__ __forceinline__ float2 load_one_smem(const unsigned char* p) {
+    if constexpr (IN == IN_CI8) {
+        const uint32_t w = *reinterpret_cast<const uint16_t*>(p);
+        return make_float2((float)(int8_t)(w & 0xff), (float)(int8_t)(w >> 8));
+    } else if constexpr (IN == IN_CI16) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+        return make_float2((float)(int16_t)(w & 0xffff), (float)(int16_t)(w >> 16));
+    } else {
+        return *reinterpret_cast<const float2*>(p);
+    }
+}
+template <int IN>
+__device__ __forceinline__ float2 load_one_global(const void* __restrict__ base, long long off) {
+    if constexpr (IN == IN_CI8) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned short*>(base) + off);
+        return make_float2((float)(int8_t)(w & 0xff), (float)(int8_t)(w >> 8));
+    } else if constexpr (IN == IN_CI16) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(base) + off);
+        return make_float2((float)(int16_t)(w & 0xffff), (float)(int16_t)(w >> 16));
+    } else {
+        return __ldg(reinterpret_cast<const float2*>(base) + off);
+    }
+}
+
 // One channel pair (4 floats) from shared memory at byte address p.
 template <int IN>
 __device__ __forceinline__ float4 load_pair_smem(const unsigned char* p) {

@@ -138,7 +138,7 @@ struct FwdArgs {
 // INV: the unnormalised inverse DFT (sign +i) computed as conj(DFT(conj(.)));
 // its last stage writes the result back into the spectrum's own row of
 // ybuf in natural order instead of to global memory.
-template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false>
+template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false, bool SMEM_OUT = false>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
@@ -151,8 +151,8 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int TOTAL = (SPW > 0 ? SPW : B) * ITEMS;
     constexpr int IPT = (TOTAL + WORKERS - 1) / WORKERS;        // items per thread
     constexpr bool EXACT = IPT * WORKERS == TOTAL;
-    static_assert(EXACT || (SPW == 0 && is_c3(C)) || (SPW > 0 && TOTAL < WORKERS),
-                  "items must divide evenly (a warp may leave lanes idle)");
+    static_assert(EXACT || (SPW == 0 && is_c3(C)) || TOTAL < WORKERS,
+                  "items must divide evenly (a warp or CTA may leave threads idle)");
     const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
     const int sp0 = SPW > 0 ? (threadIdx.x >> 5) * SPW : 0;
     auto sync = [] {
@@ -196,6 +196,15 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             float2* dst = ybuf + sp * C;
 #pragma unroll
             for (int k = 0; k < R; ++k) dst[prefix + PP * k] = make_float2(v[it][k].x, -v[it][k].y);
+        } else if constexpr (SMEM_OUT) {   // natural order, output type, row stride C elements
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if constexpr (OUT == OUT_CF32) {
+                    ybuf[sp * C + prefix + PP * k] = v[it][k];
+                } else {
+                    reinterpret_cast<__half2*>(ybuf)[sp * C + prefix + PP * k] = __float22half2_rn(v[it][k]);
+                }
+            }
         } else {
             const long long s = sb + sp;
             if (s >= vlo && s < vhi) {
@@ -460,11 +469,13 @@ pfb_fwd_kernel(FwdArgs args) {
 struct FwdInfo {
     int threads, batch, smem, stages, tap_bucket, variant;
     const void* fn;
+    int cluster;     // CTAs per thread-block cluster (0: no cluster)
 };
 
 }  // namespace ppf
 
 #include "ppf_fwd_carry.cuh"
+#include "ppf_fwd_cluster.cuh"
 
 namespace ppf {
 
@@ -473,19 +484,27 @@ inline FwdInfo fwd_info() {
     if constexpr (CarryShape<C, TM, IN>::OK) {
         using S = CarryShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4,
-                       reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT>)};
+                       reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT>), 0};
+    } else if constexpr (ClusterShape<C, TM, IN>::OK) {
+        using S = ClusterShape<C, TM, IN>;
+        return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4 | 16,
+                       reinterpret_cast<const void*>(&pfb_fwd_cluster_kernel<C, TM, IN, OUT>), S::Q};
     } else {
         using S = FwdShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, (S::RING ? 1 : 0) | (S::TW_SMEM ? 2 : 0),
-                       reinterpret_cast<const void*>(&pfb_fwd_kernel<C, TM, IN, OUT>)};
+                       reinterpret_cast<const void*>(&pfb_fwd_kernel<C, TM, IN, OUT>), 0};
     }
 }
 
+// grid: CTAs (a multiple of the cluster size for cluster kernels).
 template <int C, int TM, int IN, int OUT>
 inline cudaError_t fwd_launch(const FwdArgs& a, int grid, cudaStream_t st) {
     if constexpr (CarryShape<C, TM, IN>::OK) {
         using S = CarryShape<C, TM, IN>;
         pfb_fwd_carry_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    } else if constexpr (ClusterShape<C, TM, IN>::OK) {
+        using S = ClusterShape<C, TM, IN>;
+        pfb_fwd_cluster_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
     } else {
         using S = FwdShape<C, TM, IN>;
         pfb_fwd_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
@@ -499,7 +518,7 @@ inline bool fir_info(FwdInfo* i) {
     if constexpr (CarryShape<C, TM, IN>::OK) {
         using S = CarryShape<C, TM, IN>;
         *i = FwdInfo{S::NT, S::B, S::SMEM, 0, TM, 8,
-                     reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT_CF32, true>)};
+                     reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT_CF32, true>), 0};
         return true;
     } else {
         return false;

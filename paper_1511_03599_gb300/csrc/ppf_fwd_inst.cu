@@ -16,7 +16,8 @@ namespace ppf {
 template <int TM, int IN, int OUT>
 static bool make_entry(FwdEntry* e) {
     FwdInfo i = fwd_info<PPF_C, TM, IN, OUT>();
-    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fwd_launch<PPF_C, TM, IN, OUT>};
+    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fwd_launch<PPF_C, TM, IN, OUT>,
+                  i.cluster};
     return true;
 }
 
@@ -55,7 +56,7 @@ template <int TM, int IN>
 static bool make_fir(FwdEntry* e) {
     FwdInfo i;
     if (!fir_info<PPF_C, TM, IN>(&i)) return false;
-    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fir_launch<PPF_C, TM, IN>};
+    *e = FwdEntry{i.threads, i.batch, i.smem, i.stages, i.tap_bucket, i.variant, i.fn, &fir_launch<PPF_C, TM, IN>, 0};
     return true;
 }
 

@@ -22,9 +22,10 @@ struct FwdEntry {
     int smem;        // dynamic shared memory bytes
     int stages;      // FFT stages
     int tap_bucket;  // taps rounded up to the compiled bucket
-    int variant;     // bit 0: raw input staged by a TMA ring; bit 1: twiddles in shared memory
+    int variant;     // bit 0: TMA ring; bit 1: twiddles in smem; bit 2: halo carried; bit 4: cluster
     const void* fn;  // kernel function (for occupancy queries and attributes)
     cudaError_t (*launch)(const FwdArgs&, int grid, cudaStream_t);
+    int cluster;     // CTAs per thread-block cluster (0: none); grid counts CTAs
 };
 
 struct BwdEntry {

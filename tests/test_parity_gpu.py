@@ -74,6 +74,43 @@ def test_parity_non_power_of_two_channels(ppf, C, T, in_dtype, out_dtype):
     run_case(ppf, C, T, S, in_dtype, out_dtype, seed=4000 + C + T)
 
 
+# C >= 2048: a thread-block cluster shares each stream (one 512-channel slice
+# per CTA, the first DFT stage gathered across the cluster).  Enough spectra
+# that every cluster carries its FIR state over several batches.
+@pytest.mark.parametrize("C", [2048, 3072, 4096])
+@pytest.mark.parametrize("T,in_dtype,out_dtype", [(8, "ci8", "c64"), (4, "cf32", "c64"), (16, "ci16", "c16"),
+                                                  (1, "ci8", "c64"), (13, "ci8", "c64"), (2, "cf32", "c16")])
+def test_parity_cluster_channels(ppf, C, T, in_dtype, out_dtype):
+    S = 6 * 152 * 16 // (C // 512) + 7
+    h = synth.design_taps(C, T, scale=(1.0 / np.sqrt(C) if out_dtype == "c16" else 1.0))
+    x = synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5000 + C + T)
+    with ppf.Plan(C, T, h, in_dtype, out_dtype) as plan:
+        y = plan(to_device(x))
+        torch.cuda.synchronize()
+        idx = _sampled_indices(S, T, 96, 79 + C)
+        sel = y[torch.from_numpy(idx).cuda()]
+        assert bool(torch.isfinite(sel.float() if out_dtype == "c16" else torch.view_as_real(sel)).all())
+        got = out_to_numpy(sel, out_dtype)
+    ref = oracle.pfb_spectra(x, h, C, T, idx)
+    assert oracle.rel_l2(got, ref) <= TOL[out_dtype]
+
+
+@pytest.mark.parametrize("C", [2048, 3072, 4096])
+def test_parity_cluster_every_output_batched(ppf, C):
+    """Several independent streams in one launch (strided), every output compared."""
+    T, n_streams = 8, 3
+    S = 300
+    h = synth.design_taps(C, T)
+    xs = [synth.stream(C, S + T - 1, "ci8", 16.0, 5100 + C + i) for i in range(n_streams)]
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        got = plan.execute(torch.stack([to_device(x) for x in xs]), n_streams=n_streams)
+        torch.cuda.synchronize()
+        got = got.cpu().numpy().astype(np.complex128)
+    for i, x in enumerate(xs):
+        ref = oracle.pfb(x, h, C, T)
+        assert oracle.rel_l2(got[i], ref) <= TOL["c64"], f"stream {i}"
+
+
 @pytest.mark.parametrize("in_dtype", ["ci8", "ci16", "cf32"])
 @pytest.mark.parametrize("out_dtype", ["c64", "c16"])
 @pytest.mark.parametrize("T", [2, 4, 8, 16, 32, 64])
@@ -225,14 +262,17 @@ def test_sweep_cells_sampled(ppf, T, in_dtype, out_dtype):
     assert oracle.rel_l2(got, ref) <= TOL[out_dtype]
 
 
-def test_bounded_wait_timeout_reported_and_context_usable(ppf):
-    """A wait that nothing completes runs out, is reported, and the next launch is correct."""
-    C, T, S = 512, 8, 4096
+@pytest.mark.parametrize("C", [512, 2048])
+def test_bounded_wait_timeout_reported_and_context_usable(ppf, C):
+    """A wait that nothing completes runs out, is reported, and the next launch is correct
+    (C=2048: every CTA of each cluster gives up and the cluster leaves together)."""
+    T, S = 8, 4096
     h = synth.design_taps(C, T)
     x = synth.stream(C, S + T - 1, "ci8", 16.0, 12)
     xd = to_device(x)
     with ppf.Plan(C, T, h, "ci8", "c64") as plan:
         assert plan.info()["variant"] & 1, "expected the TMA-staged kernel for this shape"
+        assert bool(plan.info()["variant"] & 16) == (C >= 2048)
         plan.set_debug_flags(1)
         plan(xd)
         with pytest.raises(ppf.PPFError) as ei:
