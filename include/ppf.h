@@ -190,11 +190,14 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   (the autotuner's knob); synchronous.
  * ppf_beams_execute -- enqueue one queue-counter reset and ONE launch of the
  *   persistent kernel (ctas_per_sm CTAs per SM, clamped to what fits; 0 =
- *   most that fit).  Each CTA pulls tiles from the counter and runs the
- *   beam's FIR + DFT for the tile; every beam's result equals ppf_execute's.
- *   Asynchronous on `stream`; no allocation.
- * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=max CTAs
- *   per SM, [4]=SMs, [5]=dynamic shared memory bytes.
+ *   most that fit) for the beams with C <= 1024.  Each CTA pulls tiles from
+ *   the counter and runs the beam's FIR + DFT for the tile.  Then, on the
+ *   same stream, one thread-block-cluster launch per beam with C >= 2048
+ *   (the kernel ppf_execute uses for that C).  Every beam's result equals
+ *   ppf_execute's.  Asynchronous on `stream`; no allocation.
+ * ppf_beams_info -- info[0]=beams, [1]=tiles (of the persistent launch),
+ *   [2]=tile samples, [3]=max CTAs per SM, [4]=SMs, [5]=dynamic shared memory
+ *   bytes, [6]=cluster launches (beams with C >= 2048).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
  * ppf_beams_destroy -- free everything (NULL accepted).
  * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY, DEVICE_TIMEOUT.
@@ -204,7 +207,7 @@ ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C, const int
 ppf_status ppf_beams_bind(ppf_beams_t beams, const void* const* in_dev, void* const* out_dev);
 ppf_status ppf_beams_set_tiling(ppf_beams_t beams, long long tile_samples);
 ppf_status ppf_beams_execute(ppf_beams_t beams, int ctas_per_sm, ppf_stream_t stream);
-ppf_status ppf_beams_info(ppf_beams_t beams, long long info[6]);
+ppf_status ppf_beams_info(ppf_beams_t beams, long long info[7]);
 ppf_status ppf_beams_check_device(ppf_beams_t beams, ppf_stream_t stream);
 ppf_status ppf_beams_destroy(ppf_beams_t beams);
 

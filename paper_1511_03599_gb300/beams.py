@@ -77,9 +77,15 @@ class BeamSet:
         ppf.check(ppf.lib().ppf_beams_execute(self.handle, int(c), ppf._stream_handle(stream)))
 
     def info(self) -> dict:
-        a = (ctypes.c_longlong * 6)()
+        a = (ctypes.c_longlong * 7)()
         ppf.check(ppf.lib().ppf_beams_info(self.handle, a))
-        return dict(zip(("beams", "tiles", "tile_samples", "max_ctas_per_sm", "sms", "smem"), list(a)))
+        return dict(zip(("beams", "tiles", "tile_samples", "max_ctas_per_sm", "sms", "smem", "cluster_launches"),
+                        list(a)))
+
+    def launches_per_execute(self) -> int:
+        """Kernel launches one execute() enqueues (persistent + one per cluster beam)."""
+        i = self.info()
+        return (1 if i["tiles"] > 0 else 0) + i["cluster_launches"]
 
     def check_device(self, stream=None):
         ppf.check(ppf.lib().ppf_beams_check_device(self.handle, ppf._stream_handle(stream)))

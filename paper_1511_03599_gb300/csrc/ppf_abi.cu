@@ -207,23 +207,12 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     int occ = 0, grid_ctas = 0;
     if (e.cluster > 0) {
         // persistent grid: as many whole clusters as can be resident at once
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = e.cluster;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cfg.gridDim = dim3(e.cluster * sms, 1, 1);
-        cfg.blockDim = dim3(e.threads, 1, 1);
-        cfg.dynamicSmemBytes = e.smem;
-        cfg.attrs = &attr;
-        cfg.numAttrs = 1;
         int clusters = 0;
-        ce = cudaOccupancyMaxActiveClusters(&clusters, e.fn, &cfg);
+        ce = ppf::max_active_clusters(e, sms, &clusters);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: cluster occupancy");
         if (clusters < 1) return fail(PPF_ERR_UNSUPPORTED, "ppf_plan: a cluster of the kernel does not fit");
-        occ = 1;
         grid_ctas = clusters * e.cluster;
+        occ = (grid_ctas + sms - 1) / sms;   // CTAs per SM (reported)
     } else {
         ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.fn, e.threads, e.smem);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_plan: occupancy");
@@ -278,6 +267,22 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     }
     *out = p;
     return PPF_OK;
+}
+
+cudaError_t ppf::max_active_clusters(const FwdEntry& e, int sms, int* clusters) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = e.cluster;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(e.cluster * sms, 1, 1);
+    cfg.blockDim = dim3(e.threads, 1, 1);
+    cfg.dynamicSmemBytes = e.smem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    *clusters = 0;
+    return cudaOccupancyMaxActiveClusters(clusters, e.fn, &cfg);
 }
 
 // CTAs per stream: enough to fill the GPU once over all streams, at most one

@@ -8,8 +8,11 @@
 // can be captured in a CUDA graph), reads the tile's beam descriptor and runs
 // the FIR + DFT of that range with the code of the beam's (C, tap bucket)
 // class.  All classes share one block size (256 threads) and one dynamic
-// shared-memory size (the largest class's).  Complex int8 input, complex FP32
-// output: the multi-beam workload of the channeliser.
+// shared-memory size (the largest class's).  Beams with C >= 2048 whose state
+// does not fit one SM instead run, after the persistent launch and on the same
+// stream, one thread-block-cluster launch each (the single-stream kernel of
+// ppf_execute).  Complex int8 input, complex FP32 output: the multi-beam
+// workload of the channeliser.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,6 +140,15 @@ ppf_status bcuda(cudaError_t e, const char* what) {
 
 constexpr uint32_t kBeamsMagic = 0x50504642u;   // "PPFB"
 
+// The cluster kernel entry for a beam, if the beam runs on one.
+bool cluster_entry(int C, int T, ppf::FwdEntry* e) {
+    const int tm = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16;
+    bool ok = false;
+    if (C == 2048) ok = ppf::fwd_lookup_c2048(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
+    else if (C == 4096) ok = ppf::fwd_lookup_c4096(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
+    return ok && e->cluster > 0;
+}
+
 int class_of(int C, int T) {
     int ci = -1, ti = -1;
     for (int i = 0; i < ppf::kNumC; ++i)
@@ -154,6 +166,9 @@ struct ppf_beams_s {
     long long tile_samples;
     std::vector<ppf::BeamDesc> host;       // descriptors (pointers bound by ppf_beams_bind)
     std::vector<int> tm;                   // tap bucket per beam
+    std::vector<int> big;                  // beams run by a cluster launch each
+    std::vector<ppf::FwdEntry> big_entry;  // their kernels
+    std::vector<int> big_clusters;         // resident clusters of each
     ppf::BeamDesc* d_beams;
     ppf::BeamTile* d_tiles;
     long long n_tiles;
@@ -176,7 +191,10 @@ static bool valid_beams(ppf_beams_t b) {
 static ppf_status build_tiles(ppf_beams_t b, long long tile_samples) {
     std::vector<ppf::BeamTile> tiles;
     std::vector<long long> weight;
+    std::vector<bool> is_big(b->n_beams, false);
+    for (int i : b->big) is_big[i] = true;
     for (int i = 0; i < b->n_beams; ++i) {
+        if (is_big[i]) continue;
         const ppf::BeamDesc& d = b->host[i];
         const long long B = ppf::class_batch<0, 0>(d.cls);
         const long long nbt = (d.n_spectra + B - 1) / B;
@@ -296,6 +314,20 @@ extern "C" ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C
     for (int i = 0; i < n_beams; ++i) {
         b->host[i].taps = b->d_taps + taps_off[i];
         b->host[i].tw = b->d_tw + tw_off[C[i]];
+        ppf::FwdEntry e{};
+        if (!cluster_entry(C[i], T[i], &e)) continue;
+        int clusters = 0;
+        ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem);
+        if (ce == cudaSuccess) ce = ppf::max_active_clusters(e, sms, &clusters);
+        if (ce != cudaSuccess) {
+            ppf_status s = bcuda(ce, "ppf_beams_plan: cluster kernel");
+            ppf_beams_destroy(b);
+            return s;
+        }
+        if (clusters < 1) continue;   // stays on the persistent kernel
+        b->big.push_back(i);
+        b->big_entry.push_back(e);
+        b->big_clusters.push_back(clusters);
     }
     ppf_status s = build_tiles(b, 1ll << 20);
     if (s != PPF_OK) {
@@ -334,18 +366,40 @@ extern "C" ppf_status ppf_beams_execute(ppf_beams_t b, int ctas_per_sm, ppf_stre
     if (!b->bound) return ppf::set_error(PPF_ERR_INVALID_ARG, "ppf_beams_execute: buffers not bound");
     if (ctas_per_sm < 1 || ctas_per_sm > b->occupancy) ctas_per_sm = b->occupancy;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t ce = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), st);
-    if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: queue reset");
-    ppf::BeamsArgs a{b->d_beams, b->d_tiles, b->d_queue, b->d_err, b->n_tiles, 0};
-    long long grid = (long long)b->sms * ctas_per_sm;
-    if (grid > b->n_tiles) grid = b->n_tiles;
-    ppf::pfb_beams_kernel<<<(int)grid, ppf::kBeamThreads, ppf::kBeamSmem, st>>>(a);
-    ce = cudaPeekAtLastError();
-    if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: launch");
+    cudaError_t ce = cudaSuccess;
+    if (b->n_tiles > 0) {
+        ce = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), st);
+        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: queue reset");
+        ppf::BeamsArgs a{b->d_beams, b->d_tiles, b->d_queue, b->d_err, b->n_tiles, 0};
+        long long grid = (long long)b->sms * ctas_per_sm;
+        if (grid > b->n_tiles) grid = b->n_tiles;
+        ppf::pfb_beams_kernel<<<(int)grid, ppf::kBeamThreads, ppf::kBeamSmem, st>>>(a);
+        ce = cudaPeekAtLastError();
+        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: launch");
+    }
+    for (size_t j = 0; j < b->big.size(); ++j) {
+        const ppf::BeamDesc& d = b->host[b->big[j]];
+        const ppf::FwdEntry& e = b->big_entry[j];
+        ppf::FwdArgs fa;
+        fa.in = d.in;
+        fa.out = d.out;
+        fa.in_stride = 0;
+        fa.out_stride = 0;
+        const long long nb = (d.n_spectra + e.batch - 1) / e.batch;
+        fa.ctas_per_stream = (int)std::min<long long>(b->big_clusters[j], nb);   // clusters
+        fa.taps = d.taps;
+        fa.tw = d.tw;
+        fa.err = b->d_err;
+        fa.n_spectra = d.n_spectra;
+        fa.T = d.T;
+        fa.flags = 0;
+        ce = e.launch(fa, fa.ctas_per_stream * e.cluster, st);
+        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: cluster launch");
+    }
     return PPF_OK;
 }
 
-extern "C" ppf_status ppf_beams_info(ppf_beams_t b, long long info[6]) {
+extern "C" ppf_status ppf_beams_info(ppf_beams_t b, long long info[7]) {
     if (!valid_beams(b) || info == nullptr) return ppf::set_error(PPF_ERR_INVALID_ARG, "ppf_beams_info: invalid argument");
     info[0] = b->n_beams;
     info[1] = b->n_tiles;
@@ -353,6 +407,7 @@ extern "C" ppf_status ppf_beams_info(ppf_beams_t b, long long info[6]) {
     info[3] = b->occupancy;
     info[4] = b->sms;
     info[5] = ppf::kBeamSmem;
+    info[6] = (long long)b->big.size();
     return PPF_OK;
 }
 

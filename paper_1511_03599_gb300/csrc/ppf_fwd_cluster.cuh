@@ -2,9 +2,11 @@
 // (C = 2048, 3072, 4096) on a thread-block cluster.
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
-// fit one SM at these sizes, so a cluster of Q = C/512 CTAs shares a stream:
-//   * CTA q owns channels [512q, 512q+512) for the FIR (Alg. 1): each of its
-//     512 threads keeps one channel with the T-1 halo rows carried in
+// fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
+// (KS = 256 channels per CTA, two CTAs per SM, for C = 2048; KS = 512 for the
+// larger C, keeping the cluster within the portable size of 8):
+//   * CTA q owns channels [KS*q, KS*q + KS) for the FIR (Alg. 1): each of its
+//     KS threads keeps one channel with the T-1 halo rows carried in
 //     registers; raw rows arrive by TMA bulk copies of the CTA's slice of
 //     each spectrum into a double-buffered ring; the filtered slice goes to
 //     one of two slice buffers (batch parity);
@@ -30,32 +32,36 @@
 
 namespace ppf {
 
-constexpr int kSlice = 512;   // channels per CTA of a cluster
+// channels per CTA of a cluster: 256 (two CTAs per SM) where the cluster
+// stays within the portable size of 8, else 512
+constexpr int cluster_slice(int C) { return C / 256 <= 8 ? 256 : 512; }
 
-template <int C, int Q, int BIN, int B>
+template <int C, int KS, int BIN, int B>
 constexpr int cluster_smem(bool tw_smem) {
-    return 3 * B * kSlice * 8 + 2 * B * kSlice * BIN + (tw_smem ? tw_size(C) * 8 : 0) + 64;
+    return 3 * B * KS * 8 + 2 * B * KS * BIN + (tw_smem ? tw_size(C) * 8 : 0) + 64;
 }
 template <int C, int TM, int IN>
 struct ClusterShape {
-    static constexpr int Q = C >= kSlice ? C / kSlice : 1;           // CTAs per cluster
-    static constexpr int NT = kSlice;                                // one channel per thread
+    static constexpr int KS = cluster_slice(C);                      // channels per CTA
+    static constexpr int Q = C >= KS ? C / KS : 1;                   // CTAs per cluster
+    static constexpr int NT = KS;                                    // one channel per thread
+    static constexpr int MINB = KS == 256 ? 2 : 1;                   // CTAs per SM
     static constexpr int BIN = InTraits<IN>::bytes;
-    static constexpr int CAP = 226 * 1024;
+    static constexpr int CAP = KS == 256 ? 112 * 1024 + 64 : 226 * 1024;
     static constexpr int B0 = IN == IN_CI8 ? 16 : 8;
     static constexpr int BUP = Q * ((B0 + Q - 1) / Q);
     static constexpr int BDN = Q * (B0 / Q > 0 ? B0 / Q : 1);
-    static constexpr int B = cluster_smem<C, Q, BIN, BUP>(false) <= CAP ? BUP : BDN;   // spectra per batch
+    static constexpr int B = cluster_smem<C, KS, BIN, BUP>(false) <= CAP ? BUP : BDN;   // spectra per batch
     static constexpr int SPC = B / Q;                                // spectra each CTA transforms
-    static constexpr int YLB = B * kSlice * 8;                       // one slice buffer == stage buffer
-    static constexpr int SLOTB = B * kSlice * BIN;                   // raw rows of the slice
-    static constexpr bool TW_SMEM = cluster_smem<C, Q, BIN, B>(true) <= CAP;
+    static constexpr int YLB = B * KS * 8;                           // one slice buffer == stage buffer
+    static constexpr int SLOTB = B * KS * BIN;                       // raw rows of the slice
+    static constexpr bool TW_SMEM = cluster_smem<C, KS, BIN, B>(true) <= CAP;
     static constexpr int WK_OFF = 2 * YLB;
     static constexpr int TW_OFF = 3 * YLB;
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
     static constexpr bool OK = (C == 2048 || C == 3072 || C == 4096) && Q <= 8 && TM <= 16 && B >= TM - 1 &&
-                               SPC * C == B * kSlice && SMEM <= CAP;
+                               SPC * C == B * KS && SMEM <= CAP;
 };
 
 // Split cluster barrier: arrive (release: this thread's earlier writes, e.g.
@@ -84,7 +90,7 @@ __device__ __forceinline__ float2 dsmem_ld_f2(uint32_t addr) {
 // First DFT stage of the CTA's SPC spectra: gather the columns from the
 // filtered slices of all CTAs of the cluster (rb[r]: shared::cluster address
 // of CTA r's slice), radix-R DFT, inter-stage twiddles.  Results stay in v.
-template <int C, int SPC, int NT, int Q, int IPT>
+template <int C, int KS, int SPC, int NT, int Q, int IPT>
 __device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], float2 (&v)[IPT][fft_radix(C, 0)],
                                                     const float2* __restrict__ tws, bool tw_smem, int q) {
     constexpr int R = fft_radix(C, 0);
@@ -96,15 +102,15 @@ __device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], flo
         const int item = tid + it * NT;
         if (item >= TOTAL) break;
         const int sp = item / NN, b = item % NN;
-        const uint32_t row = (uint32_t)(q * SPC + sp) * (kSlice * 8);   // batch row of the spectrum
+        const uint32_t row = (uint32_t)(q * SPC + sp) * (KS * 8);       // batch row of the spectrum
 #pragma unroll
         for (int a = 0; a < R; ++a) {
-            if constexpr (kSlice % NN == 0) {  // column a lies in one slice for every b
-                constexpr int PER = kSlice / NN;
+            if constexpr (KS % NN == 0) {      // column a lies in one slice for every b
+                constexpr int PER = KS / NN;
                 v[it][a] = dsmem_ld_f2(rb[a / PER] + row + (uint32_t)(((a % PER) * NN + b) * 8));
             } else {                           // the slice depends on b
                 const int c = NN * a + b;
-                v[it][a] = dsmem_ld_f2(dsmem_map(rb[0], (uint32_t)(c / kSlice)) + row + (uint32_t)((c % kSlice) * 8));
+                v[it][a] = dsmem_ld_f2(dsmem_map(rb[0], (uint32_t)(c / KS)) + row + (uint32_t)((c % KS) * 8));
             }
         }
     }
@@ -139,10 +145,10 @@ __device__ __forceinline__ void cluster_stage0_store(const float2 (&v)[IPT][fft_
 }
 
 template <int C, int TM, int IN, int OUT>
-__global__ void __cluster_dims__(ClusterShape<C, TM, IN>::Q, 1, 1) __launch_bounds__(ClusterShape<C, TM, IN>::NT, 1)
+__global__ void __cluster_dims__(ClusterShape<C, TM, IN>::Q, 1, 1) __launch_bounds__(ClusterShape<C, TM, IN>::NT, ClusterShape<C, TM, IN>::MINB)
 pfb_fwd_cluster_kernel(FwdArgs args) {
     using S = ClusterShape<C, TM, IN>;
-    constexpr int NT = S::NT, B = S::B, BIN = S::BIN, Q = S::Q, SPC = S::SPC;
+    constexpr int NT = S::NT, B = S::B, BIN = S::BIN, Q = S::Q, SPC = S::SPC, kSlice = S::KS;
     constexpr int NST = fft_stages(C);
     static_assert(NST == 3, "the pipelined loop runs stage 1 before the barrier and stage 2 after it");
     constexpr int R0 = fft_radix(C, 0);
@@ -290,7 +296,7 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
             uint32_t rbk[Q];
 #pragma unroll
             for (int r = 0; r < Q; ++r) rbk[r] = rb[r] + off;
-            cluster_stage0_load<C, SPC, NT, Q, IPT0>(rbk, v, tws, S::TW_SMEM, q);
+            cluster_stage0_load<C, kSlice, SPC, NT, Q, IPT0>(rbk, v, tws, S::TW_SMEM, q);
             cluster_stage0_store<C, SPC, NT, IPT0>(v, wk);   // stage 2 of batch k-1 has read wk
         }
         // (the next iteration's first CTA barrier orders these writes before stage 1)

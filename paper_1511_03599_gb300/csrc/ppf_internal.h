@@ -28,6 +28,10 @@ struct FwdEntry {
     int cluster;     // CTAs per thread-block cluster (0: none); grid counts CTAs
 };
 
+// Resident clusters of a cluster kernel entry (persistent grid): the most
+// whole clusters of e.cluster CTAs that fit at once (0: none fits).
+cudaError_t max_active_clusters(const FwdEntry& e, int sms, int* clusters);
+
 struct BwdEntry {
     int threads;     // threads per CTA
     int batch;       // raw rows per CTA batch

@@ -99,3 +99,28 @@ def test_beams_reject_unsupported(mods):
         beams.BeamSet([32], [8], [10], [synth.design_taps(32, 8)])
     with pytest.raises(ppf.PPFError):
         beams.BeamSet([512], [32], [10], [synth.design_taps(512, 32)])
+
+
+def test_beams_large_channel_counts_use_cluster_launches(mods):
+    """C >= 2048 beams run the single-stream cluster kernel: bit-identical to ppf_execute,
+    one launch each; a set of only such beams has no persistent launch at all."""
+    ppf, _ = mods
+    for beams_def in ([(2048, 8, 300), (4096, 4, 100), (512, 8, 200), (2048, 16, 57)],
+                      [(2048, 3, 129), (4096, 16, 64)]):
+        bs, xs, taps, ins, outs = make_set(mods, beams_def, seed=120)
+        n_big = sum(1 for c, _, _ in beams_def if c >= 2048)
+        info = bs.info()
+        assert info["cluster_launches"] == n_big
+        assert bs.launches_per_execute() == n_big + (1 if info["tiles"] > 0 else 0)
+        assert (info["tiles"] > 0) == any(c < 2048 for c, _, _ in beams_def)
+        bs.execute()
+        torch.cuda.synchronize()
+        bs.check_device()
+        for (c, t, s), x, h, xd, y in zip(beams_def, xs, taps, ins, outs):
+            assert oracle.rel_l2(y.cpu().numpy(), oracle.pfb(x, h, c, t)) <= 1e-5, (c, t, s)
+            if c >= 2048:
+                with ppf.Plan(c, t, h, "ci8", "c64") as plan:
+                    ref = plan(xd)
+                    torch.cuda.synchronize()
+                assert torch.equal(torch.view_as_real(ref), torch.view_as_real(y)), (c, t, s)
+        bs.close()
