@@ -148,9 +148,8 @@ ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* i
  * plan memory, and the call allocates nothing.  The plan itself (made once
  * at set-up with ppf_plan) still owns the taps and tables.
  *   - Size limit: each CTA needs a row of tap_bucket*C floats; the call uses
- *     fewer CTAs when the array is short and returns PPF_ERR_UNSUPPORTED when
- *     even one CTA per stream does not fit (n_streams * tap_bucket * C >
- *     1,048,576).
+ *     at most 1,048,576 / (tap_bucket*C) CTAs (256 at C=256, T=16).  CTAs
+ *     share the batches of all streams, so every stream count fits.
  *   - The first call on a device looks up the array's device address with
  *     that device current (cudaGetSymbolAddress); make that first call before
  *     any stream capture.

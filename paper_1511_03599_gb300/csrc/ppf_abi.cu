@@ -285,10 +285,11 @@ cudaError_t ppf::max_active_clusters(const FwdEntry& e, int sms, int* clusters) 
     return cudaOccupancyMaxActiveClusters(clusters, e.fn, &cfg);
 }
 
-// CTAs per stream: enough to fill the GPU once over all streams, at most one
-// per batch of a stream.
+// CTAs per stream: as many as fit in ONE wave of `target` resident CTAs over
+// all streams (rounding up would start a partial second wave that doubles the
+// time of the CTAs in it), at least one, at most one per batch of a stream.
 static int ctas_per_stream(long long target, long long n_streams, long long batches) {
-    long long cps = (target + n_streams - 1) / n_streams;
+    long long cps = target / n_streams;
     if (cps > batches) cps = batches;
     if (cps < 1) cps = 1;
     return (int)cps;
@@ -370,9 +371,8 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
                                 (unsigned long long)(n_streams * in_len * 8)))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps the input");
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
-    const int cps = ctas_per_stream((long long)p->sms * p->bwd_occupancy, n_streams, nb);
-    const long long grid = (long long)cps * n_streams;
-    if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: too many streams");
+    // one wave of resident CTAs sharing the batches of all streams equally
+    const long long grid = std::min<long long>((long long)p->sms * p->bwd_occupancy, nb * n_streams);
     if (grid > p->partials_ctas) {   // scratch for the per-CTA tap-gradient partial sums
         if (p->d_partials) cudaFree(p->d_partials);
         p->d_partials = nullptr;
@@ -392,8 +392,8 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
     a.n_spectra = n_spectra;
     a.gY_stride = out_len;
     a.x_stride = in_len;
+    a.n_streams = n_streams;
     a.T = T;
-    a.ctas_per_stream = cps;
     a.flags = p->debug_flags;
     cudaError_t ce = p->bwd.launch(a, (int)grid, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: launch");
@@ -587,17 +587,12 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     // one row of TM*C partial sums per CTA; fewer CTAs per stream if the array is short
     const long long row = (long long)TM * C;
     const long long max_ctas = PPF_NOALLOC_PARTIALS_FLOATS / row;
-    if (n_streams > max_ctas)
-        return fail(PPF_ERR_UNSUPPORTED,
-                    "ppf_backward_noalloc: %lld streams need %lld partial sums, more than the fixed %d",
-                    n_streams, n_streams * row, PPF_NOALLOC_PARTIALS_FLOATS);
     float* partials = nullptr;
     ppf_status st = noalloc_scratch(p->device, &partials);
     if (st != PPF_OK) return st;
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
-    int cps = ctas_per_stream((long long)p->sms * p->bwd_occupancy, n_streams, nb);
-    if ((long long)cps * n_streams > max_ctas) cps = (int)(max_ctas / n_streams);
-    const long long grid = (long long)cps * n_streams;
+    const long long grid =
+        std::min<long long>(std::min<long long>((long long)p->sms * p->bwd_occupancy, nb * n_streams), max_ctas);
     ppf::BwdArgs a;
     a.gY = static_cast<const float2*>(grad_out_dev);
     a.x = static_cast<const float2*>(in_dev);
@@ -609,8 +604,8 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     a.n_spectra = n_spectra;
     a.gY_stride = out_len;
     a.x_stride = in_len;
+    a.n_streams = n_streams;
     a.T = T;
-    a.ctas_per_stream = cps;
     a.flags = p->debug_flags;
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t ce = p->bwd.launch(a, (int)grid, cs);

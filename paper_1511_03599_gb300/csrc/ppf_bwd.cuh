@@ -9,10 +9,13 @@
 //   grad_x[r][c] = sum_t h[t][c] g_y[r-t][c]            (transposed FIR)
 //   grad_h[t][c] = sum_r Re(conj(g_y[r-t][c]) x[r][c])  (tap correlation)
 // with g_y[s] = 0 outside 0 <= s < S.  Both sums run over raw rows r, so the
-// work is partitioned by r: each CTA owns a contiguous range of raw rows,
-// needs g_y rows back to r-(T-1) (carried in registers from the previous
-// batch, or from one leading batch it inverse-transforms at its start), and
-// writes every grad_x row of its range exactly once.  The tap gradient is
+// work is partitioned by r: the batches of raw rows of all streams form one
+// sequence (stream-major) and each CTA owns an equal contiguous share of it,
+// which may span stream boundaries (every CTA of the grid busy whatever the
+// stream count).  Within each stream segment of its share the CTA needs g_y
+// rows back to r-(T-1) (carried in registers from the previous batch, or
+// from one leading batch it inverse-transforms at the segment's start), and
+// writes every grad_x row of the segment exactly once.  The tap gradient is
 // accumulated per thread in registers, written as one partial per CTA, and
 // summed over CTAs in a fixed order by a second kernel (deterministic: no
 // floating-point atomics).
@@ -49,8 +52,8 @@ struct BwdArgs {
     int* err;
     long long n_spectra;
     long long gY_stride, x_stride;   // samples between streams
+    long long n_streams;
     int T;
-    int ctas_per_stream;
     int flags;
 };
 
@@ -69,17 +72,12 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
     const long long n_spectra = args.n_spectra;
     const int T = args.T;
     const long long n_raw = n_spectra + T - 1;
-    const long long nbt = (n_raw + B - 1) / B;        // batches of raw rows
-    const int cps = args.ctas_per_stream;
-    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
-    const float2* gY = args.gY + (size_t)strm * args.gY_stride;
-    const float2* x = args.x + (size_t)strm * args.x_stride;
-    float2* gx = args.gx ? args.gx + (size_t)strm * args.x_stride : nullptr;
-    const long long lo = (long long)bx * nbt / cps;
-    const long long hi = (long long)(bx + 1) * nbt / cps;
-    const long long nb = hi - lo;
+    const long long nbt = (n_raw + B - 1) / B;        // batches of raw rows per stream
+    const long long U = nbt * args.n_streams;          // batches of all streams
+    const long long u0 = (long long)blockIdx.x * U / gridDim.x;
+    const long long u1 = (long long)(blockIdx.x + 1) * U / gridDim.x;
 
-    // taps of channel c as (h, h) pairs; tap-gradient accumulators
+    // taps of channel c as (h, h) pairs; tap-gradient accumulators (over all segments)
     unsigned long long hh[TM], acch[TM];
 #pragma unroll
     for (int t = 0; t < TM; ++t) {
@@ -87,123 +85,138 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         hh[t] = pk2(h, h);
         acch[t] = 0ull;
     }
-    unsigned long long carry[TM > 1 ? TM - 1 : 1];     // g_y rows (first row) - (TM-1) .. -1
-#pragma unroll
-    for (int i = 0; i < TM - 1; ++i) carry[i] = 0ull;
-
-    // iterations: k = k0 (a leading batch that only fills the carry) .. nb-1
-    const long long k0 = (lo > 0 && TM > 1) ? -1 : 0;
-    const long long nit = nb - k0;
-    auto g_rows = [&](long long j) -> long long {     // valid G rows of absolute batch j
-        const long long r = n_spectra - j * B;
-        return r <= 0 ? 0 : (r < B ? r : B);
-    };
-    auto x_rows = [&](long long j) -> long long {
-        const long long r = n_raw - j * B;
-        return r <= 0 ? 0 : (r < B ? r : B);
-    };
-    // G slots and their barriers are indexed by the iteration it; x slots by the
-    // x batch k (there is no x batch in the leading iteration), so each slot's
-    // n-th use waits for phase n of its own barrier.
-    auto issue = [&](long long it) {                   // iteration it = k - k0
-        const long long k = it + k0, j = lo + k;
-        const int q = (int)(it & 1);
-        const long long gr = g_rows(j);
-        if (gr > 0) {
-            mbar_expect_tx(&bars[q], (uint32_t)(gr * C * 8));
-            tma_load_1d(gslot + q * B * C, gY + (size_t)j * B * C, (uint32_t)(gr * C * 8), &bars[q]);
-        }
-        const long long xr = k >= 0 ? x_rows(j) : 0;
-        if (xr > 0) {
-            const int qx = (int)(k & 1);
-            mbar_expect_tx(&bars[2 + qx], (uint32_t)(xr * C * 8));
-            tma_load_1d(xslot + qx * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + qx]);
-        }
-    };
-    auto wait_it = [&](long long it, uint64_t limit) -> bool {
-        const long long k = it + k0, j = lo + k;
-        bool ok = true;
-        if (g_rows(j) > 0) ok = ok && mbar_wait_bounded(&bars[it & 1], (uint32_t)((it >> 1) & 1), limit);
-        if (k >= 0 && x_rows(j) > 0)
-            ok = ok && mbar_wait_bounded(&bars[2 + (k & 1)], (uint32_t)((k >> 1) & 1), limit);
-        return ok;
-    };
     if (c == 0) {
         for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
         *sflag = 0;
     }
     __syncthreads();
-    if (nb <= 0) {                                     // no rows: contribute zero partials
-        for (int t = 0; t < TM; ++t) args.partials[(size_t)blockIdx.x * TM * C + t * C + c] = 0.f;
-        return;
-    }
-    if (c == 0) {
-        issue(0);
-        if (nit > 1) issue(1);
-    }
 
-    for (long long it = 0; it < nit; ++it) {
-        const long long k = it + k0, j = lo + k;
-        const int q = (int)(it & 1);
-        float2* gs = gslot + q * B * C;
-        const float2* xs = xslot + (k & 1) * B * C;
-        if (c == 0) {
-            bool ok = wait_it(it, kWaitLimitNs);
-            if (it == 0 && (args.flags & FWD_INJECT_TIMEOUT)) ok = ok && mbar_wait_bounded(&bars[4], 0, kInjectedWaitNs);
-            if (!ok) {
-                for (long long i2 = it; i2 < it + 2 && i2 < nit; ++i2) wait_it(i2, kWaitLimitNs);
-                atomicExch(args.err, 1);
-                *sflag = 1;
+    // Uses of the G slots and of the x slots in earlier segments: slot use n
+    // (counted over the whole kernel) waits for phase n of its barrier.
+    long long gbase = 0, xbase = 0;
+    for (long long u = u0; u < u1;) {
+        const long long strm = u / nbt;
+        const long long lo = u - strm * nbt;
+        const long long hi = (u1 - strm * nbt < nbt) ? u1 - strm * nbt : nbt;
+        u = strm * nbt + hi;
+        const long long nb = hi - lo;
+        const float2* gY = args.gY + (size_t)strm * args.gY_stride;
+        const float2* x = args.x + (size_t)strm * args.x_stride;
+        float2* gx = args.gx ? args.gx + (size_t)strm * args.x_stride : nullptr;
+
+        unsigned long long carry[TM > 1 ? TM - 1 : 1];     // g_y rows (first row) - (TM-1) .. -1
+#pragma unroll
+        for (int i = 0; i < TM - 1; ++i) carry[i] = 0ull;
+
+        // iterations: k = k0 (a leading batch that only fills the carry) .. nb-1
+        const long long k0 = (lo > 0 && TM > 1) ? -1 : 0;
+        const long long nit = nb - k0;
+        auto g_rows = [&](long long j) -> long long {     // valid G rows of absolute batch j
+            const long long r = n_spectra - j * B;
+            return r <= 0 ? 0 : (r < B ? r : B);
+        };
+        auto x_rows = [&](long long j) -> long long {
+            const long long r = n_raw - j * B;
+            return r <= 0 ? 0 : (r < B ? r : B);
+        };
+        // G slots are indexed by the iteration it; x slots by the x batch k
+        // (there is no x batch in the leading iteration).  Every use of a
+        // slot completes one phase of its barrier, also a use with nothing to
+        // copy (the last batch of a stream may hold no G row): the arrival
+        // then expects zero bytes, so uses and phases stay in step across
+        // the segments of the CTA's share.
+        auto issue = [&](long long it) {                   // iteration it = k - k0
+            const long long k = it + k0, j = lo + k;
+            const int q = (int)((gbase + it) & 1);
+            const long long gr = g_rows(j);
+            mbar_expect_tx(&bars[q], (uint32_t)(gr * C * 8));
+            if (gr > 0) tma_load_1d(gslot + q * B * C, gY + (size_t)j * B * C, (uint32_t)(gr * C * 8), &bars[q]);
+            if (k >= 0) {
+                const long long xr = x_rows(j);
+                const int qx = (int)((xbase + k) & 1);
+                mbar_expect_tx(&bars[2 + qx], (uint32_t)(xr * C * 8));
+                if (xr > 0)
+                    tma_load_1d(xslot + qx * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + qx]);
             }
+        };
+        auto wait_it = [&](long long it, uint64_t limit) -> bool {
+            const long long k = it + k0;
+            const long long gn = gbase + it, xn = xbase + k;
+            bool ok = mbar_wait_bounded(&bars[gn & 1], (uint32_t)((gn >> 1) & 1), limit);
+            if (k >= 0) ok = mbar_wait_bounded(&bars[2 + (xn & 1)], (uint32_t)((xn >> 1) & 1), limit) && ok;
+            return ok;
+        };
+        if (c == 0) {
+            fence_proxy_async_smem();   // slots written by an earlier segment's inverse DFT
+            issue(0);
+            if (nit > 1) issue(1);
         }
-        __syncthreads();
-        if (*sflag) return;
-        // g_y = F^H G for the B rows of the batch, in place (warp-local stages)
-        static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, false, S::SPW, true>(gs, args.tw, nullptr, 0, 0, 0);
-        });
-        __syncthreads();
-        // one thread per channel: sequence g_i = carried rows (i < TM-1) then the batch rows
-        const long long row0 = j * B;                  // first raw row (and G row) of the batch
-        unsigned long long gxa[B];
-#pragma unroll
-        for (int r = 0; r < B; ++r) gxa[r] = 0ull;
-        unsigned long long gseq[B + TM - 1];
-#pragma unroll
-        for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
-#pragma unroll
-        for (int r = 0; r < B; ++r) {
-            const float2 g = (row0 + r < n_spectra) ? gs[r * C + c] : make_float2(0.f, 0.f);
-            gseq[TM - 1 + r] = pk2(g.x, g.y);
-        }
-        if (k >= 0) {
-#pragma unroll
-            for (int r = 0; r < B; ++r) {
-                const float2 xv = (row0 + r < n_raw) ? xs[r * C + c] : make_float2(0.f, 0.f);
-                const unsigned long long xp = pk2(xv.x, xv.y);
-#pragma unroll
-                for (int t = 0; t < TM; ++t) {
-                    if (t < T) {
-                        const unsigned long long g = gseq[TM - 1 + r - t];
-                        ffma2(gxa[r], hh[t], g);        // grad_x[r] += h[t] g_y[r-t]
-                        ffma2(acch[t], g, xp);          // (g.re x.re, g.im x.im)
-                    }
+
+        for (long long it = 0; it < nit; ++it) {
+            const long long k = it + k0, j = lo + k;
+            float2* gs = gslot + ((gbase + it) & 1) * B * C;
+            const float2* xs = xslot + ((xbase + k) & 1) * B * C;
+            if (c == 0) {
+                bool ok = wait_it(it, kWaitLimitNs);
+                if (gbase == 0 && it == 0 && (args.flags & FWD_INJECT_TIMEOUT))
+                    ok = ok && mbar_wait_bounded(&bars[4], 0, kInjectedWaitNs);
+                if (!ok) {
+                    for (long long i2 = it; i2 < it + 2 && i2 < nit; ++i2) wait_it(i2, kWaitLimitNs);
+                    atomicExch(args.err, 1);
+                    *sflag = 1;
                 }
             }
-            if (gx != nullptr) {
+            __syncthreads();
+            if (*sflag) return;
+            // g_y = F^H G for the B rows of the batch, in place (warp-local stages)
+            static_for<NST>([&](auto p) {
+                fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, false, S::SPW, true>(gs, args.tw, nullptr, 0, 0, 0);
+            });
+            __syncthreads();
+            // one thread per channel: sequence g_i = carried rows (i < TM-1) then the batch rows
+            const long long row0 = j * B;                  // first raw row (and G row) of the batch
+            unsigned long long gxa[B];
 #pragma unroll
-                for (int r = 0; r < B; ++r)
-                    if (row0 + r < n_raw) gx[(size_t)(row0 + r) * C + c] = upk2(gxa[r]);
+            for (int r = 0; r < B; ++r) gxa[r] = 0ull;
+            unsigned long long gseq[B + TM - 1];
+#pragma unroll
+            for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                const float2 g = (row0 + r < n_spectra) ? gs[r * C + c] : make_float2(0.f, 0.f);
+                gseq[TM - 1 + r] = pk2(g.x, g.y);
+            }
+            if (k >= 0) {
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    const float2 xv = (row0 + r < n_raw) ? xs[r * C + c] : make_float2(0.f, 0.f);
+                    const unsigned long long xp = pk2(xv.x, xv.y);
+#pragma unroll
+                    for (int t = 0; t < TM; ++t) {
+                        if (t < T) {
+                            const unsigned long long g = gseq[TM - 1 + r - t];
+                            ffma2(gxa[r], hh[t], g);        // grad_x[r] += h[t] g_y[r-t]
+                            ffma2(acch[t], g, xp);          // (g.re x.re, g.im x.im)
+                        }
+                    }
+                }
+                if (gx != nullptr) {
+#pragma unroll
+                    for (int r = 0; r < B; ++r)
+                        if (row0 + r < n_raw) gx[(size_t)(row0 + r) * C + c] = upk2(gxa[r]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < TM - 1; ++i) carry[i] = gseq[B + i];
+            __syncthreads();
+            if (c == 0 && it + 2 < nit) {
+                fence_proxy_async_smem();
+                issue(it + 2);
             }
         }
-#pragma unroll
-        for (int i = 0; i < TM - 1; ++i) carry[i] = gseq[B + i];
-        __syncthreads();
-        if (c == 0 && it + 2 < nit) {
-            fence_proxy_async_smem();
-            issue(it + 2);
-        }
+        gbase += nit;
+        xbase += nb;
     }
     float* part = args.partials + (size_t)blockIdx.x * TM * C;
 #pragma unroll
