@@ -37,7 +37,8 @@ struct BwdShape {
     static constexpr int SLOTB = B * C * 8;                          // complex FP32 rows of a batch
     static constexpr int NWARP = NT / 32;
     static constexpr int SPW = NWARP > 0 ? B / NWARP : 0;            // spectra per warp in the DFT
-    static constexpr int SMEM = 4 * SLOTB + 64;                      // G slots, x slots, barriers
+    static constexpr int TWB = tw_size(C) * 8;                       // twiddle tables
+    static constexpr int SMEM = 4 * SLOTB + TWB + 64;                // G slots, x slots, twiddles, barriers
     static constexpr bool OK = (C >= 64 && C <= 256) && (TM <= 16) && (B >= TM - 1) &&
                                SPW >= 1 && SPW * NWARP == B && fft_items_fit(C, SPW, 32);
 };
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
     extern __shared__ __align__(128) unsigned char smem[];
     float2* gslot = reinterpret_cast<float2*>(smem);                    // [2][B][C]
     float2* xslot = reinterpret_cast<float2*>(smem + 2 * S::SLOTB);     // [2][B][C]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * S::SLOTB);  // g0 g1 x0 x1 never
+    float2* tw_s = reinterpret_cast<float2*>(smem + 4 * S::SLOTB);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * S::SLOTB + S::TWB);  // g0 g1 x0 x1 never
     volatile int* sflag = reinterpret_cast<volatile int*>(bars + 5);
 
     const int c = threadIdx.x;
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         hh[t] = pk2(h, h);
         acch[t] = 0ull;
     }
+    for (int i = c; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
     if (c == 0) {
         for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
             if (*sflag) return;
             // g_y = F^H G for the B rows of the batch, in place (warp-local stages)
             static_for<NST>([&](auto p) {
-                fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, false, S::SPW, true>(gs, args.tw, nullptr, 0, 0, 0);
+                fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, true, S::SPW, true>(gs, tw_s, nullptr, 0, 0, 0);
             });
             __syncthreads();
             // one thread per channel: sequence g_i = carried rows (i < TM-1) then the batch rows
@@ -182,29 +185,58 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
             unsigned long long gseq[B + TM - 1];
 #pragma unroll
             for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
-#pragma unroll
-            for (int r = 0; r < B; ++r) {
-                const float2 g = (row0 + r < n_spectra) ? gs[r * C + c] : make_float2(0.f, 0.f);
-                gseq[TM - 1 + r] = pk2(g.x, g.y);
-            }
-            if (k >= 0) {
+            const float2* gsc = gs + c;
+            const float2* xsc = xs + c;
+            if (row0 + B <= n_spectra && T == TM) {        // whole batch, every tap: no checks
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
-                    const float2 xv = (row0 + r < n_raw) ? xs[r * C + c] : make_float2(0.f, 0.f);
-                    const unsigned long long xp = pk2(xv.x, xv.y);
+                    const float2 g = gsc[r * C];
+                    gseq[TM - 1 + r] = pk2(g.x, g.y);
+                }
+                if (k >= 0) {
 #pragma unroll
-                    for (int t = 0; t < TM; ++t) {
-                        if (t < T) {
+                    for (int r = 0; r < B; ++r) {
+                        const float2 xv = xsc[r * C];
+                        const unsigned long long xp = pk2(xv.x, xv.y);
+#pragma unroll
+                        for (int t = 0; t < TM; ++t) {
                             const unsigned long long g = gseq[TM - 1 + r - t];
-                            ffma2(gxa[r], hh[t], g);        // grad_x[r] += h[t] g_y[r-t]
-                            ffma2(acch[t], g, xp);          // (g.re x.re, g.im x.im)
+                            ffma2(gxa[r], hh[t], g);
+                            ffma2(acch[t], g, xp);
                         }
                     }
-                }
-                if (gx != nullptr) {
+                    if (gx != nullptr) {
+                        float2* gxr = gx + (size_t)row0 * C + c;
 #pragma unroll
-                    for (int r = 0; r < B; ++r)
-                        if (row0 + r < n_raw) gx[(size_t)(row0 + r) * C + c] = upk2(gxa[r]);
+                        for (int r = 0; r < B; ++r) gxr[r * C] = upk2(gxa[r]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < B; ++r) {
+                    const float2 g = (row0 + r < n_spectra) ? gsc[r * C] : make_float2(0.f, 0.f);
+                    gseq[TM - 1 + r] = pk2(g.x, g.y);
+                }
+                if (k >= 0) {
+#pragma unroll
+                    for (int r = 0; r < B; ++r) {
+                        const float2 xv = (row0 + r < n_raw) ? xsc[r * C] : make_float2(0.f, 0.f);
+                        const unsigned long long xp = pk2(xv.x, xv.y);
+#pragma unroll
+                        for (int t = 0; t < TM; ++t) {
+                            if (t < T) {
+                                const unsigned long long g = gseq[TM - 1 + r - t];
+                                ffma2(gxa[r], hh[t], g);        // grad_x[r] += h[t] g_y[r-t]
+                                ffma2(acch[t], g, xp);          // (g.re x.re, g.im x.im)
+                            }
+                        }
+                    }
+                    if (gx != nullptr) {
+                        float2* gxr = gx + (size_t)row0 * C + c;
+#pragma unroll
+                        for (int r = 0; r < B; ++r)
+                            if (row0 + r < n_raw) gxr[r * C] = upk2(gxa[r]);
+                    }
                 }
             }
 #pragma unroll
