@@ -2,6 +2,7 @@
 // selection, device tables, launches, the host-buffer pipeline and errors.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -285,14 +286,11 @@ cudaError_t ppf::max_active_clusters(const FwdEntry& e, int sms, int* clusters) 
     return cudaOccupancyMaxActiveClusters(clusters, e.fn, &cfg);
 }
 
-// CTAs per stream: as many as fit in ONE wave of `target` resident CTAs over
-// all streams (rounding up would start a partial second wave that doubles the
-// time of the CTAs in it), at least one, at most one per batch of a stream.
-static int ctas_per_stream(long long target, long long n_streams, long long batches) {
-    long long cps = target / n_streams;
-    if (cps > batches) cps = batches;
-    if (cps < 1) cps = 1;
-    return (int)cps;
+// Work units (CTAs, or clusters of CTAs) of one launch: one wave of resident
+// units sharing the batches of all streams equally, at most one per batch.
+static long long work_units(long long resident, long long n_streams, long long batches_per_stream) {
+    const long long total = n_streams * batches_per_stream;
+    return std::max<long long>(1, std::min<long long>(resident, total));
 }
 
 static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, long long in_stride, void* out_dev,
@@ -310,9 +308,17 @@ static ppf_status launch_fwd(ppf_plan_t p, const void* in_dev, long long in_stri
     a.flags = p->debug_flags;
     const long long nb = (n + p->fwd.batch - 1) / p->fwd.batch;
     const int unit = p->fwd.cluster > 0 ? p->fwd.cluster : 1;      // CTAs per work unit
-    a.ctas_per_stream = ctas_per_stream(p->grid / unit, n_streams, nb);
-    const long long grid = (long long)a.ctas_per_stream * n_streams * unit;
-    if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: too many streams");
+    a.n_streams = n_streams;
+    long long grid;
+    if ((p->fwd.variant & 4) && p->fwd.cluster == 0) {
+        // carry kernel: the same number of CTAs on every stream, one wave if
+        // the streams allow it (at least one CTA, at most one per batch)
+        const long long cps = std::max<long long>(1, std::min<long long>(p->grid / n_streams, nb));
+        grid = cps * n_streams;
+        if (grid > 0x7fffffffll) return fail(PPF_ERR_INVALID_ARG, "ppf_execute: too many streams");
+    } else {
+        grid = work_units(p->grid / unit, n_streams, nb) * unit;
+    }
     cudaError_t ce = p->fwd.launch(a, (int)grid, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute: launch");
     return PPF_OK;
@@ -372,7 +378,7 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps the input");
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
     // one wave of resident CTAs sharing the batches of all streams equally
-    const long long grid = std::min<long long>((long long)p->sms * p->bwd_occupancy, nb * n_streams);
+    const long long grid = work_units((long long)p->sms * p->bwd_occupancy, n_streams, nb);
     if (grid > p->partials_ctas) {   // scratch for the per-CTA tap-gradient partial sums
         if (p->d_partials) cudaFree(p->d_partials);
         p->d_partials = nullptr;
@@ -591,8 +597,7 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     ppf_status st = noalloc_scratch(p->device, &partials);
     if (st != PPF_OK) return st;
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
-    const long long grid =
-        std::min<long long>(std::min<long long>((long long)p->sms * p->bwd_occupancy, nb * n_streams), max_ctas);
+    const long long grid = std::min<long long>(work_units((long long)p->sms * p->bwd_occupancy, n_streams, nb), max_ctas);
     ppf::BwdArgs a;
     a.gY = static_cast<const float2*>(grad_out_dev);
     a.x = static_cast<const float2*>(in_dev);
@@ -645,8 +650,8 @@ extern "C" ppf_status ppf_fir(ppf_plan_t p, const void* in_dev, void* y_dev, lon
     a.T = p->T;
     a.flags = p->debug_flags;
     const long long nb = (n_spectra + p->fir.batch - 1) / p->fir.batch;
-    a.ctas_per_stream = ctas_per_stream(p->fir_grid, 1, nb);
-    cudaError_t ce = p->fir.launch(a, a.ctas_per_stream, reinterpret_cast<cudaStream_t>(stream));
+    a.n_streams = 1;
+    cudaError_t ce = p->fir.launch(a, (int)work_units(p->fir_grid, 1, nb), reinterpret_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_fir: launch");
     return PPF_OK;
 }

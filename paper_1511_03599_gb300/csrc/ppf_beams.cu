@@ -69,7 +69,7 @@ __device__ __forceinline__ bool beam_tile(const BeamsArgs& a, const BeamDesc& d,
     fa.out = d.out;
     fa.in_stride = 0;
     fa.out_stride = 0;
-    fa.ctas_per_stream = 1;
+    fa.n_streams = 1;
     fa.taps = d.taps;
     fa.tw = d.tw;
     fa.err = a.err;
@@ -386,14 +386,15 @@ extern "C" ppf_status ppf_beams_execute(ppf_beams_t b, int ctas_per_sm, ppf_stre
         fa.in_stride = 0;
         fa.out_stride = 0;
         const long long nb = (d.n_spectra + e.batch - 1) / e.batch;
-        fa.ctas_per_stream = (int)std::min<long long>(b->big_clusters[j], nb);   // clusters
+        fa.n_streams = 1;
+        const long long clusters = std::min<long long>(b->big_clusters[j], nb);
         fa.taps = d.taps;
         fa.tw = d.tw;
         fa.err = b->d_err;
         fa.n_spectra = d.n_spectra;
         fa.T = d.T;
         fa.flags = 0;
-        ce = e.launch(fa, fa.ctas_per_stream * e.cluster, st);
+        ce = e.launch(fa, (int)(clusters * e.cluster), st);
         if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: cluster launch");
     }
     return PPF_OK;

@@ -121,7 +121,9 @@ struct FwdArgs {
     void* out;               // n_spectra*C outputs per stream
     long long in_stride;     // samples between consecutive input streams
     long long out_stride;    // samples between consecutive output streams
-    int ctas_per_stream;     // CTAs that share one stream (grid = streams * this)
+    long long n_streams;     // streams; the carry kernel splits the grid evenly over them (the grid is a
+                             // multiple of n_streams), the others share the batches of all streams
+                             // equally among their work units (CTAs, or clusters)
     const float* taps;       // TM*C floats, tap-major, rows >= T are zero
     const float2* tw;        // twiddle tables, tw_size(C) entries
     int* err;                // device status word: 1 = a bounded wait gave up
@@ -448,21 +450,38 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
     return true;
 }
 
+// The batches of all streams form one sequence (stream-major, nbt per stream);
+// work unit `unit` of `n_units` owns the equal contiguous share [u0, u1),
+// which it walks as segments [lo, hi) of single streams.
+struct BatchShare {
+    long long nbt, u, u1;
+    __device__ __forceinline__ BatchShare(long long nbt_, long long n_streams, int unit, int n_units)
+        : nbt(nbt_), u((long long)unit * (nbt_ * n_streams) / n_units),
+          u1((long long)(unit + 1) * (nbt_ * n_streams) / n_units) {}
+    // next segment: stream and batch range; false when the share is done
+    __device__ __forceinline__ bool next(long long& strm, long long& lo, long long& hi) {
+        if (u >= u1) return false;
+        strm = u / nbt;
+        lo = u - strm * nbt;
+        hi = (u1 - strm * nbt < nbt) ? u1 - strm * nbt : nbt;
+        u = strm * nbt + hi;
+        return true;
+    }
+};
+
 template <int C, int TM, int IN, int OUT>
 __global__ void __launch_bounds__(FwdShape<C, TM, IN>::NT, FwdShape<C, TM, IN>::NT == 256 ? 2 : 1)
 pfb_fwd_kernel(FwdArgs args) {
     using S = FwdShape<C, TM, IN>;
     extern __shared__ __align__(128) unsigned char smem[];
-    // stream of this CTA and its contiguous range of batches within the stream:
-    // raw spectra stream through the CTA once
-    const long long nbt = (args.n_spectra + S::B - 1) / S::B;
-    const int cps = args.ctas_per_stream;
-    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
-    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * S::BIN;
-    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
-    const long long lo = (long long)bx * nbt / cps;
-    const long long hi = (long long)(bx + 1) * nbt / cps;
-    fwd_range<C, TM, IN, OUT>(args, in, out, lo, hi, smem);
+    // the CTA's share of the batches: raw spectra stream through the CTA once
+    BatchShare share((args.n_spectra + S::B - 1) / S::B, args.n_streams, blockIdx.x, gridDim.x);
+    long long strm, lo, hi;
+    while (share.next(strm, lo, hi)) {
+        const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * S::BIN;
+        void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
+        if (!fwd_range<C, TM, IN, OUT>(args, in, out, lo, hi, smem)) return;
+    }
 }
 
 // Host side: shape + launch of one instantiation.

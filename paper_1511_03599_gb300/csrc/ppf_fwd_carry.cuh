@@ -138,7 +138,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
     const int D = TM - T;                            // leading zero taps of the bucket
     const long long n_raw = n_spectra + T - 1;
     const long long nbt = (n_spectra + B - 1) / B;
-    const int cps = args.ctas_per_stream;
+    const int cps = (int)(gridDim.x / args.n_streams);   // CTAs per stream (the grid is a multiple)
     const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
     const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
     void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);

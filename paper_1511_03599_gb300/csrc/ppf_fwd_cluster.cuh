@@ -170,17 +170,6 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
     const int D = TM - T;
     const long long n_raw = n_spectra + T - 1;
     const long long nbt = (n_spectra + B - 1) / B;
-    const int cps = args.ctas_per_stream;            // clusters per stream
-    const int cl = blockIdx.x / Q;
-    const int strm = cl / cps, bx = cl - strm * cps;
-    const unsigned char* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
-    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * OB;
-    const long long lo = (long long)bx * nbt / cps;
-    const long long hi = (long long)(bx + 1) * nbt / cps;
-    const long long nb = hi - lo;                    // the same for every CTA of the cluster
-    if (nb <= 0) return;                             // (uniform over the cluster)
-    const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
-    const long long nraw_b = (T > 1) ? nb + 1 : nb;
 
     const float2* tws = args.tw;
     if constexpr (S::TW_SMEM) {
@@ -193,113 +182,135 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
         const float x = (t >= D) ? __ldg(args.taps + (t - D) * C + q * kSlice + tid) : 0.f;
         h[t] = pk2(x, x);
     }
-    float2 carry[TM > 1 ? TM - 1 : 1];
-#pragma unroll
-    for (int i = 0; i < TM - 1; ++i) {
-        const long long r = lo * B - (TM - 1) + i;
-        carry[i] = (r >= 0 && r < n_raw) ? load_one_global<IN>(in, r * C + q * kSlice + tid) : make_float2(0.f, 0.f);
-    }
     uint32_t rb[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) rb[r] = dsmem_map(smem_addr(ylb), (uint32_t)r);
-
-    auto rows_of = [&](long long j) -> long long {
-        const long long r = n_raw - (lo + j) * B;
-        return r <= 0 ? 0 : (r < B ? r : B);
-    };
-    // raw batch j: the CTA's slice of rows [(lo+j)B, (lo+j)B + B), one bulk copy per row
-    auto issue = [&](long long j) {
-        const long long rows = rows_of(j);
-        if (rows > 0) {
-            uint64_t* bar = &bars[j & 1];
-            mbar_expect_tx(bar, (uint32_t)(rows * kSlice * BIN));
-            unsigned char* dst = ring + (j & 1) * S::SLOTB;
-            const unsigned char* src = in + ((size_t)(lo + j) * B * C + (size_t)q * kSlice) * BIN;
-            for (long long r = 0; r < rows; ++r)
-                tma_load_1d(dst + r * kSlice * BIN, src + (size_t)r * C * BIN, kSlice * BIN, bar);
-        }
-    };
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
         *sdead = 0;
     }
     __syncthreads();
-    if (tid == 0) {
-        issue(0);
-        if (nraw_b > 1) issue(1);
-    }
 
-    // iteration k: FIR of batch k (k < nraw_b), later stages of batch k-1 (k >= 1)
-    for (long long k = 0; k <= nraw_b; ++k) {
-        const bool fir = k < nraw_b;
-        if (!fir) __syncthreads();   // the gathered batch is complete in wk
-        if (fir) {
-            // ------------------------------------------------ wait for slot k
-            if (tid == 0 && !*sdead) {
-                bool ok = rows_of(k) == 0 || mbar_wait_bounded(&bars[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
-                if (k == 0 && (args.flags & FWD_INJECT_TIMEOUT))
-                    ok = ok && mbar_wait_bounded(&bars[2], 0, kInjectedWaitNs);
-                if (!ok) {
-                    for (long long j = k; j < k + 2 && j < nraw_b; ++j)
-                        if (rows_of(j) > 0) mbar_wait_bounded(&bars[j & 1], (uint32_t)((j >> 1) & 1), kWaitLimitNs);
-                    atomicExch(args.err, 1);
-                    *sdead = 1;
-                }
-            }
-            __syncthreads();
-            const bool dead = *sdead != 0;
-            // ------------------------------------------------------ FIR
-            unsigned long long acc[B];
-            if (!dead) {
-                const unsigned char* slot = ring + (k & 1) * S::SLOTB + tid * BIN;
+    // The cluster's share of the batches of all streams (the same for every
+    // CTA of the cluster), walked as single-stream segments.  kb counts the
+    // raw batches of earlier segments: raw batch k of a segment is use kb + k
+    // of the ring slot (kb + k) & 1 and of the slice buffer (kb + k) & 1;
+    // every ring use completes one phase of its slot's barrier (zero bytes
+    // when it has no rows), so slots, phases and slice buffers run on across
+    // segments.
+    BatchShare share(nbt, args.n_streams, blockIdx.x / Q, gridDim.x / Q);
+    long long strm, lo, hi, kb = 0;
+    while (share.next(strm, lo, hi)) {
+        const unsigned char* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
+        void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * OB;
+        const long long nb = hi - lo;
+        const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
+        const long long nraw_b = (T > 1) ? nb + 1 : nb;
+
+        float2 carry[TM > 1 ? TM - 1 : 1];
 #pragma unroll
-                for (int j = 0; j < B; ++j) acc[j] = 0ull;
-                float2 nxt[TM > 1 ? TM - 1 : 1];
-#pragma unroll
-                for (int i = 0; i < B + TM - 1; ++i) {
-                    const float2 x = (i < TM - 1) ? carry[i < TM - 1 ? i : 0]
-                                                  : load_one_smem<IN>(slot + (size_t)(i - (TM - 1)) * kSlice * BIN);
-                    const unsigned long long xx = pk2(x.x, x.y);
-#pragma unroll
-                    for (int j = 0; j < B; ++j) {
-                        const int t = i - j;
-                        if (t >= 0 && t < TM) {
-                            if (IN != IN_CF32 || t >= D) ffma2(acc[j], h[t], xx);
-                        }
+        for (int i = 0; i < TM - 1; ++i) {
+            const long long r = lo * B - (TM - 1) + i;
+            carry[i] = (r >= 0 && r < n_raw) ? load_one_global<IN>(in, r * C + q * kSlice + tid)
+                                             : make_float2(0.f, 0.f);
+        }
+        auto rows_of = [&](long long j) -> long long {
+            const long long r = n_raw - (lo + j) * B;
+            return r <= 0 ? 0 : (r < B ? r : B);
+        };
+        // raw batch j: the CTA's slice of rows [(lo+j)B, (lo+j)B + B), one bulk copy per row
+        auto issue = [&](long long j) {
+            const long long rows = rows_of(j);
+            const long long u = kb + j;
+            uint64_t* bar = &bars[u & 1];
+            mbar_expect_tx(bar, (uint32_t)(rows * kSlice * BIN));
+            unsigned char* dst = ring + (u & 1) * S::SLOTB;
+            const unsigned char* src = in + ((size_t)(lo + j) * B * C + (size_t)q * kSlice) * BIN;
+            for (long long r = 0; r < rows; ++r)
+                tma_load_1d(dst + r * kSlice * BIN, src + (size_t)r * C * BIN, kSlice * BIN, bar);
+        };
+        auto wait_use = [&](long long j, uint64_t limit) -> bool {
+            const long long u = kb + j;
+            return mbar_wait_bounded(&bars[u & 1], (uint32_t)((u >> 1) & 1), limit);
+        };
+        if (tid == 0 && !*sdead) {
+            fence_proxy_async_smem();   // the slots were last read by an earlier segment's FIR
+            issue(0);
+            if (nraw_b > 1) issue(1);
+        }
+
+        // iteration k: FIR of batch k (k < nraw_b), later stages of batch k-1 (k >= 1)
+        for (long long k = 0; k <= nraw_b; ++k) {
+            const bool fir = k < nraw_b;
+            if (!fir) __syncthreads();   // the gathered batch is complete in wk
+            if (fir) {
+                // ------------------------------------------------ wait for slot k
+                if (tid == 0 && !*sdead) {
+                    bool ok = wait_use(k, kWaitLimitNs);
+                    if (kb == 0 && k == 0 && (args.flags & FWD_INJECT_TIMEOUT))
+                        ok = ok && mbar_wait_bounded(&bars[2], 0, kInjectedWaitNs);
+                    if (!ok) {
+                        for (long long j = k; j < k + 2 && j < nraw_b; ++j) wait_use(j, kWaitLimitNs);
+                        atomicExch(args.err, 1);
+                        *sdead = 1;
                     }
-                    if (i >= B) nxt[i - B] = x;
                 }
+                __syncthreads();
+                const bool dead = *sdead != 0;
+                // ------------------------------------------------------ FIR
+                unsigned long long acc[B];
+                if (!dead) {
+                    const unsigned char* slot = ring + ((kb + k) & 1) * S::SLOTB + tid * BIN;
 #pragma unroll
-                for (int i = 0; i < TM - 1; ++i) carry[i] = nxt[i];
-            }
-            __syncthreads();
-            if (tid == 0 && !dead && k + 2 < nraw_b) {   // slot k is free: refill it
-                fence_proxy_async_smem();
-                issue(k + 2);
-            }
-            if (!dead) {
-                float2* yl = ylb + (k & 1) * (B * kSlice);
+                    for (int j = 0; j < B; ++j) acc[j] = 0ull;
+                    float2 nxt[TM > 1 ? TM - 1 : 1];
 #pragma unroll
-                for (int j = 0; j < B; ++j) yl[j * kSlice + tid] = upk2(acc[j]);
+                    for (int i = 0; i < B + TM - 1; ++i) {
+                        const float2 x = (i < TM - 1) ? carry[i < TM - 1 ? i : 0]
+                                                      : load_one_smem<IN>(slot + (size_t)(i - (TM - 1)) * kSlice * BIN);
+                        const unsigned long long xx = pk2(x.x, x.y);
+#pragma unroll
+                        for (int j = 0; j < B; ++j) {
+                            const int t = i - j;
+                            if (t >= 0 && t < TM) {
+                                if (IN != IN_CF32 || t >= D) ffma2(acc[j], h[t], xx);
+                            }
+                        }
+                        if (i >= B) nxt[i - B] = x;
+                    }
+#pragma unroll
+                    for (int i = 0; i < TM - 1; ++i) carry[i] = nxt[i];
+                }
+                __syncthreads();
+                if (tid == 0 && !dead && k + 2 < nraw_b) {   // slot k is free: refill it
+                    fence_proxy_async_smem();
+                    issue(k + 2);
+                }
+                if (!dead) {
+                    float2* yl = ylb + ((kb + k) & 1) * (B * kSlice);
+#pragma unroll
+                    for (int j = 0; j < B; ++j) yl[j * kSlice + tid] = upk2(acc[j]);
+                }
             }
+            const long long sbp = (lo + k - 1) * B - (T - 1) + q * SPC;   // first output spectrum of batch k-1
+            const long long pvlo = *sdead ? vhi : vlo;                      // a CTA that gave up stores nothing
+            if (k >= 1) fft_stage<C, SPC, NT, 1, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
+            if (fir) cluster_arrive();     // slices of batch k written; gathers of batch k-1 done
+            if (k >= 1) fft_stage<C, SPC, NT, 2, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
+            if (fir) {
+                cluster_wait();
+                float2 v[IPT0][R0];
+                const uint32_t off = (uint32_t)(((kb + k) & 1) * (B * kSlice * 8));
+                uint32_t rbk[Q];
+#pragma unroll
+                for (int r = 0; r < Q; ++r) rbk[r] = rb[r] + off;
+                cluster_stage0_load<C, kSlice, SPC, NT, Q, IPT0>(rbk, v, tws, S::TW_SMEM, q);
+                cluster_stage0_store<C, SPC, NT, IPT0>(v, wk);   // stage 2 of batch k-1 has read wk
+            }
+            // (the next iteration's first CTA barrier orders these writes before stage 1)
         }
-        const long long sbp = (lo + k - 1) * B - (T - 1) + q * SPC;   // first output spectrum of batch k-1
-        const long long pvlo = *sdead ? vhi : vlo;                      // a CTA that gave up stores nothing
-        if (k >= 1) fft_stage<C, SPC, NT, 1, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
-        if (fir) cluster_arrive();     // slices of batch k written; gathers of batch k-1 done
-        if (k >= 1) fft_stage<C, SPC, NT, 2, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
-        if (fir) {
-            cluster_wait();
-            float2 v[IPT0][R0];
-            const uint32_t off = (uint32_t)((k & 1) * (B * kSlice * 8));
-            uint32_t rbk[Q];
-#pragma unroll
-            for (int r = 0; r < Q; ++r) rbk[r] = rb[r] + off;
-            cluster_stage0_load<C, kSlice, SPC, NT, Q, IPT0>(rbk, v, tws, S::TW_SMEM, q);
-            cluster_stage0_store<C, SPC, NT, IPT0>(v, wk);   // stage 2 of batch k-1 has read wk
-        }
-        // (the next iteration's first CTA barrier orders these writes before stage 1)
+        kb += nraw_b;
     }
     cluster_arrive();   // no CTA leaves while a peer may still gather from it
     cluster_wait();

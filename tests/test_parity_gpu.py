@@ -111,6 +111,27 @@ def test_parity_cluster_every_output_batched(ppf, C):
         assert oracle.rel_l2(got[i], ref) <= TOL["c64"], f"stream {i}"
 
 
+# Several streams in one launch with more batches than work units, so shares
+# of the batch sequence cross stream boundaries (carry, generic and cluster
+# kernels): bit-identical to one launch per stream, and right by the oracle.
+@pytest.mark.parametrize("C,T,in_dtype,S,ns", [(512, 8, "ci8", 2000, 5), (256, 16, "cf32", 1500, 7),
+                                               (4096, 16, "cf32", 400, 3), (2048, 8, "ci8", 700, 4),
+                                               (64, 1, "ci16", 3000, 9)])
+def test_batched_shares_cross_streams(ppf, C, T, in_dtype, S, ns):
+    h = synth.design_taps(C, T)
+    xs = [synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5200 + C + i) for i in range(ns)]
+    with ppf.Plan(C, T, h, in_dtype, "c64") as plan:
+        yb = plan.execute(torch.stack([to_device(x) for x in xs]), n_streams=ns)
+        torch.cuda.synchronize()
+        plan.check_device()
+        for i, x in enumerate(xs):
+            yi = plan(to_device(x))
+            torch.cuda.synchronize()
+            assert torch.equal(torch.view_as_real(yb[i]), torch.view_as_real(yi)), f"stream {i}"
+        y1 = yb[1].cpu().numpy().astype(np.complex128)
+    assert oracle.rel_l2(y1, oracle.pfb(xs[1], h, C, T)) <= TOL["c64"]
+
+
 @pytest.mark.parametrize("in_dtype", ["ci8", "ci16", "cf32"])
 @pytest.mark.parametrize("out_dtype", ["c64", "c16"])
 @pytest.mark.parametrize("T", [2, 4, 8, 16, 32, 64])
