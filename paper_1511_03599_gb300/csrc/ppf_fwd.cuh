@@ -69,6 +69,18 @@ __device__ __forceinline__ int phys(int i) {
         constexpr int R = fft_radix(C, P);
         constexpr int RPG = R >= 16 ? 1 : 16 / R;   // rows sharing one 16-element bank group
         return i ^ (((i / R) / RPG) & (R - 1));
+    } else if constexpr (P > 0) {
+        // A middle stage reads, per prefix row of N_P elements, R groups of
+        // NN = N_{P+1} consecutive elements.  With NN < 16 one half-warp spans
+        // G = 16/NN rows whose groups fall on the same banks; XOR the group
+        // index with the row index mod G so they fall on different ones.
+        constexpr int NP = fft_n(C, P), R = fft_radix(C, P), NN = NP / R;
+        if constexpr (NN < 16 && 16 / NN <= R && (NN & (NN - 1)) == 0 && (R & (R - 1)) == 0) {
+            constexpr int G = 16 / NN;
+            return i ^ (((i / NP) % G) * NN);
+        } else {
+            return i;
+        }
     } else {
         return i;
     }
