@@ -62,10 +62,23 @@ constexpr int fft_n(int C, int p) {
 // R = R_last elements, read column-wise by lanes walking consecutive rows
 // and written row-wise) is XOR-swizzled within each row so both access
 // patterns hit 16 distinct 8-byte bank pairs per half-warp.
-template <int C, int P>
+//
+// LAYOUT 1 pads the rows of that last buffer instead (row stride R + 1, an
+// odd number of elements, also conflict-free for both patterns): every
+// access is then a per-lane base plus a compile-time offset, with no XOR per
+// access.  It needs a spectrum span of C + C/R elements (spec_span); the
+// carry kernel picks the layout per shape.
+constexpr int last_radix(int C) { return fft_radix(C, fft_stages(C) - 1); }
+template <int C, int LAYOUT>
+constexpr int spec_span() { return LAYOUT == 1 ? C + C / last_radix(C) : C; }
+
+template <int C, int P, int LAYOUT = 0>
 __device__ __forceinline__ int phys(int i) {
     constexpr int NST = fft_stages(C);
-    if constexpr (P > 0 && P == NST - 1) {
+    if constexpr (P > 0 && P == NST - 1 && LAYOUT == 1) {
+        constexpr int R = fft_radix(C, P);
+        return (i / R) * (R + 1) + i % R;
+    } else if constexpr (P > 0 && P == NST - 1) {
         constexpr int R = fft_radix(C, P);
         constexpr int RPG = R >= 16 ? 1 : 16 / R;   // rows sharing one 16-element bank group
         return i ^ (((i / R) / RPG) & (R - 1));
@@ -152,7 +165,8 @@ struct FwdArgs {
 // INV: the unnormalised inverse DFT (sign +i) computed as conj(DFT(conj(.)));
 // its last stage writes the result back into the spectrum's own row of
 // ybuf in natural order instead of to global memory.
-template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false, bool SMEM_OUT = false>
+template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false, bool SMEM_OUT = false,
+          int LAYOUT = 0>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
@@ -165,6 +179,8 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int TOTAL = (SPW > 0 ? SPW : B) * ITEMS;
     constexpr int IPT = (TOTAL + WORKERS - 1) / WORKERS;        // items per thread
     constexpr bool EXACT = IPT * WORKERS == TOTAL;
+    constexpr int SPAN = spec_span<C, LAYOUT>();   // elements per spectrum in ybuf
+    static_assert(!(LAYOUT == 1 && (INV || SMEM_OUT)), "padded rows only for the forward stores to HBM");
     static_assert(EXACT || (SPW == 0 && is_c3(C)) || TOTAL < WORKERS,
                   "items must divide evenly (a warp or CTA may leave threads idle)");
     const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
@@ -181,10 +197,10 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         if (!EXACT && item >= TOTAL) break;
         const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
-        const float2* src = ybuf + sp * C;
+        const float2* src = ybuf + sp * SPAN;
 #pragma unroll
         for (int a = 0; a < R; ++a) {
-            v[it][a] = src[phys<C, P>(prefix * NP + NN * a + b)];
+            v[it][a] = src[phys<C, P, LAYOUT>(prefix * NP + NN * a + b)];
             if constexpr (INV && P == 0) v[it][a].y = -v[it][a].y;
         }
     }
@@ -203,9 +219,9 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
                 const float2 w = TW_SMEM ? twp[k * NN + b] : __ldg(twp + k * NN + b);
                 v[it][k] = cmul(v[it][k], w);
             }
-            float2* dst = ybuf + sp * C;
+            float2* dst = ybuf + sp * SPAN;
 #pragma unroll
-            for (int k = 0; k < R; ++k) dst[phys<C, P + 1>((prefix + PP * k) * NN + b)] = v[it][k];
+            for (int k = 0; k < R; ++k) dst[phys<C, P + 1, LAYOUT>((prefix + PP * k) * NN + b)] = v[it][k];
         } else if constexpr (INV) {
             float2* dst = ybuf + sp * C;
 #pragma unroll

@@ -50,7 +50,12 @@ struct CarryCand {
     static constexpr int NT = C / 2;                                 // one channel pair per thread
     static constexpr int B = B_;
     static constexpr int BIN = InTraits<IN>::bytes;
-    static constexpr int YBYTES = B * C * 8;
+    // last DFT stage's buffer: padded rows (no per-access index arithmetic)
+    // where they measured faster -- C <= 128, and 16 taps at C <= 256 --
+    // else the XOR swizzle (C = 512/1024 at T <= 8 lost 2-4 % with padding)
+    static constexpr int LAYOUT = (C <= 128 || (TM >= 16 && C <= 256)) ? 1 : 0;
+    static constexpr int YSPAN = spec_span<C, LAYOUT>();             // elements per spectrum in ybuf
+    static constexpr int YBYTES = B * YSPAN * 8;
     static constexpr int SLOTB = B * C * BIN;
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BASE = YBYTES + 2 * SLOTB + 64;
@@ -258,7 +263,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
 #pragma unroll
                 for (int j = 0; j < B; ++j) {
                     const float2 a = upk2(acc[j][0]), b = upk2(acc[j][1]);
-                    *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
+                    *reinterpret_cast<float4*>(ybuf + j * S::YSPAN + 2 * cp) = make_float4(a.x, a.y, b.x, b.y);
                 }
             }
         }
@@ -272,7 +277,8 @@ pfb_fwd_carry_kernel(FwdArgs args) {
         if constexpr (!FIRONLY) {
             const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
             static_for<NST>([&](auto p) {
-                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW>(ybuf, tws, out, sb, vlo, vhi);
+                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW, false, false, S::LAYOUT>(
+                    ybuf, tws, out, sb, vlo, vhi);
             });
         }
     }
