@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-beams", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)   # internal: one timed oracle run
     return ap.parse_args()
 
 
@@ -300,9 +301,34 @@ def cpu_baseline(w, target_s: float):
     S = int(max(256, min(w.S, S * target_s / max(dt, 1e-3))))
     dt = run(S)
     cores = os.cpu_count()
-    return {"value": w.C * S / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{S} of {w.S} spectra of {w.name} (FP64 direct FIR + naive O(C^2) DFT, numpy)",
-            "seconds": dt}
+    res = {"value": w.C * S / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{S} of {w.S} spectra of {w.name} (FP64 direct FIR + naive O(C^2) DFT, numpy)",
+           "seconds": dt}
+    # the same oracle on one core: a child process with every BLAS / OpenMP pool at one thread
+    try:
+        s1 = max(64, S // max(1, cores) // 2)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(s1),
+                            "--in-dtype", w.in_dtype, "--spectra", str(w.S)],
+                           env=env, capture_output=True, text=True, timeout=600)
+        d1 = json.loads(r.stdout.strip().splitlines()[-1])
+        res["single_core"] = {"value": w.C * s1 / d1["seconds"] / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"{s1} of {w.S} spectra", "seconds": d1["seconds"]}
+    except Exception as e:  # noqa: BLE001 - context beside the metric
+        res["single_core"] = {"error": str(e)}
+    return res
+
+
+def oracle_sample(w, S: int):
+    """One timed oracle run on S spectra (the child process of the single-core baseline)."""
+    import oracle
+    from paper_1511_03599_gb300 import synth
+    x = synth.stream(w.C, S + w.T - 1, w.in_dtype, w.sigma, w.seed, w.tones)
+    h = w.taps()
+    t0 = time.perf_counter()
+    oracle.pfb(x, h, w.C, w.T)
+    print(json.dumps({"seconds": time.perf_counter() - t0}), flush=True)
 
 
 def cpu_fast(w, target_s: float):
@@ -370,6 +396,9 @@ def main():
     args = parse()
     from paper_1511_03599_gb300 import synth
     w = synth.target_workload(args.in_dtype, args.spectra)
+    if args.oracle_sample > 0:
+        oracle_sample(w, args.oracle_sample)
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -451,6 +480,27 @@ def main():
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
                "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, 2-stream chunk pipeline"}
+        # the host link alone: the same bytes copied concurrently (D2H of the
+        # output, H2D of the input) with no kernel -- the bound of this number
+        try:
+            s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+            def copies():
+                with torch.cuda.stream(s1):
+                    yh.copy_(y, non_blocking=True)
+                with torch.cuda.stream(s2):
+                    x.copy_(xh, non_blocking=True)   # the same values back into the input buffer
+            copies()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                copies()
+            torch.cuda.synchronize()
+            tc = (time.perf_counter() - t0) / n_e2e
+            e2e["copy_only_ms"] = tc * 1e3
+            e2e["frac_of_copy_only"] = tc / te
+        except Exception as e:  # noqa: BLE001 - context only
+            e2e["copy_only_error"] = str(e)
         del xh, yh
 
     abl = None
