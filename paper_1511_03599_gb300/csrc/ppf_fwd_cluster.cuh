@@ -1,10 +1,10 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
-// (C = 2048, 3072, 4096) on a thread-block cluster.
+// (C = 2048, 3072, 4096, and most C = 768 shapes) on a thread-block cluster.
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
-// (KS = 256 channels per CTA, two CTAs per SM, for C = 2048; KS = 512 for the
-// larger C, keeping the cluster within the portable size of 8):
+// (KS = 256 channels per CTA, two CTAs per SM, up to C = 2048; KS = 512 for
+// the larger C, keeping the cluster within the portable size of 8):
 //   * CTA q owns channels [KS*q, KS*q + KS) for the FIR (Alg. 1): each of its
 //     KS threads keeps one channel with the T-1 halo rows carried in
 //     registers; raw rows arrive by TMA bulk copies of the CTA's slice of
@@ -17,8 +17,8 @@
 //     remaining stages run there and the last one stores the spectra.
 // The loop is software-pipelined by one batch with ONE cluster barrier per
 // batch, split into arrive and wait: iteration k filters batch k into slice
-// buffer k&1, arrives, runs the later DFT stages of batch k-1, waits, and
-// gathers batch k.  The barrier of iteration k publishes the slices of batch
+// buffer k&1, runs the middle DFT stages of batch k-1, arrives, runs the
+// last stage of batch k-1, waits, and gathers batch k.  The barrier of iteration k publishes the slices of batch
 // k and certifies that every gather of batch k-1 is done, so the slice buffer
 // that batch k+1 overwrites is no longer read by anyone.  A last barrier after
 // the loop keeps every CTA resident until no peer reads its shared memory.
@@ -60,7 +60,10 @@ struct ClusterShape {
     static constexpr int TW_OFF = 3 * YLB;
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
-    static constexpr bool OK = (C == 2048 || C == 3072 || C == 4096) && Q <= 8 && TM <= 16 && B >= TM - 1 &&
+    // where it measured faster than the single-CTA kernels: C >= 2048, and
+    // C = 768 except 8-tap int8 (C = 1024 fp32 and C = 1536 were slower)
+    static constexpr bool WANTED = C >= 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8));
+    static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
 };
 
@@ -150,7 +153,7 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
     using S = ClusterShape<C, TM, IN>;
     constexpr int NT = S::NT, B = S::B, BIN = S::BIN, Q = S::Q, SPC = S::SPC, kSlice = S::KS;
     constexpr int NST = fft_stages(C);
-    static_assert(NST == 3, "the pipelined loop runs stage 1 before the barrier and stage 2 after it");
+    static_assert(NST >= 2, "the pipelined loop runs the middle stages before the barrier and the last after it");
     constexpr int R0 = fft_radix(C, 0);
     constexpr int IPT0 = (SPC * (C / R0) + NT - 1) / NT;
     constexpr int OB = OUT == OUT_CF32 ? 8 : 4;
@@ -295,9 +298,13 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
             }
             const long long sbp = (lo + k - 1) * B - (T - 1) + q * SPC;   // first output spectrum of batch k-1
             const long long pvlo = *sdead ? vhi : vlo;                      // a CTA that gave up stores nothing
-            if (k >= 1) fft_stage<C, SPC, NT, 1, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
+            if (k >= 1) {                  // middle DFT stages of batch k-1
+                static_for<NST - 2>([&](auto pm1) {
+                    fft_stage<C, SPC, NT, decltype(pm1)::value + 1, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
+                });
+            }
             if (fir) cluster_arrive();     // slices of batch k written; gathers of batch k-1 done
-            if (k >= 1) fft_stage<C, SPC, NT, 2, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
+            if (k >= 1) fft_stage<C, SPC, NT, NST - 1, OUT, S::TW_SMEM>(wk, tws, out, sbp, pvlo, vhi);
             if (fir) {
                 cluster_wait();
                 float2 v[IPT0][R0];

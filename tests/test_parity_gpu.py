@@ -77,11 +77,11 @@ def test_parity_non_power_of_two_channels(ppf, C, T, in_dtype, out_dtype):
 # C >= 2048: a thread-block cluster shares each stream (one 512-channel slice
 # per CTA, the first DFT stage gathered across the cluster).  Enough spectra
 # that every cluster carries its FIR state over several batches.
-@pytest.mark.parametrize("C", [2048, 3072, 4096])
+@pytest.mark.parametrize("C", [768, 1024, 1536, 2048, 3072, 4096])
 @pytest.mark.parametrize("T,in_dtype,out_dtype", [(8, "ci8", "c64"), (4, "cf32", "c64"), (16, "ci16", "c16"),
                                                   (1, "ci8", "c64"), (13, "ci8", "c64"), (2, "cf32", "c16")])
 def test_parity_cluster_channels(ppf, C, T, in_dtype, out_dtype):
-    S = 6 * 152 * 16 // (C // 512) + 7
+    S = 6 * 152 * 16 // max(1, C // 512) + 7
     h = synth.design_taps(C, T, scale=(1.0 / np.sqrt(C) if out_dtype == "c16" else 1.0))
     x = synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5000 + C + T)
     with ppf.Plan(C, T, h, in_dtype, out_dtype) as plan:
@@ -95,7 +95,7 @@ def test_parity_cluster_channels(ppf, C, T, in_dtype, out_dtype):
     assert oracle.rel_l2(got, ref) <= TOL[out_dtype]
 
 
-@pytest.mark.parametrize("C", [2048, 3072, 4096])
+@pytest.mark.parametrize("C", [768, 1024, 2048, 3072, 4096])
 def test_parity_cluster_every_output_batched(ppf, C):
     """Several independent streams in one launch (strided), every output compared."""
     T, n_streams = 8, 3
