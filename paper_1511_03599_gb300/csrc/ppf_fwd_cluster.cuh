@@ -92,9 +92,12 @@ __device__ __forceinline__ float2 dsmem_ld_f2(uint32_t addr) {
 
 // First DFT stage of the CTA's SPC spectra: gather the columns from the
 // filtered slices of all CTAs of the cluster (rb[r]: shared::cluster address
-// of CTA r's slice), radix-R DFT, inter-stage twiddles.  Results stay in v.
+// of CTA r's slice; local: shared::cta address of this CTA's own slice, the
+// address `mapa` maps to another rank), radix-R DFT, inter-stage twiddles.
+// Results stay in v.
 template <int C, int KS, int SPC, int NT, int Q, int IPT>
-__device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], float2 (&v)[IPT][fft_radix(C, 0)],
+__device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], uint32_t local,
+                                                    float2 (&v)[IPT][fft_radix(C, 0)],
                                                     const float2* __restrict__ tws, bool tw_smem, int q) {
     constexpr int R = fft_radix(C, 0);
     constexpr int NN = C / R;                  // N_1
@@ -113,7 +116,7 @@ __device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], flo
                 v[it][a] = dsmem_ld_f2(rb[a / PER] + row + (uint32_t)(((a % PER) * NN + b) * 8));
             } else {                           // the slice depends on b
                 const int c = NN * a + b;
-                v[it][a] = dsmem_ld_f2(dsmem_map(rb[0], (uint32_t)(c / KS)) + row + (uint32_t)((c % KS) * 8));
+                v[it][a] = dsmem_ld_f2(dsmem_map(local + row + (uint32_t)((c % KS) * 8), (uint32_t)(c / KS)));
             }
         }
     }
@@ -312,7 +315,7 @@ pfb_fwd_cluster_kernel(FwdArgs args) {
                 uint32_t rbk[Q];
 #pragma unroll
                 for (int r = 0; r < Q; ++r) rbk[r] = rb[r] + off;
-                cluster_stage0_load<C, kSlice, SPC, NT, Q, IPT0>(rbk, v, tws, S::TW_SMEM, q);
+                cluster_stage0_load<C, kSlice, SPC, NT, Q, IPT0>(rbk, smem_addr(ylb) + off, v, tws, S::TW_SMEM, q);
                 cluster_stage0_store<C, SPC, NT, IPT0>(v, wk);   // stage 2 of batch k-1 has read wk
             }
             // (the next iteration's first CTA barrier orders these writes before stage 1)
