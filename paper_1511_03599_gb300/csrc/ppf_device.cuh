@@ -241,6 +241,23 @@ __device__ __forceinline__ float4 load_pair_global(const void* __restrict__ base
     }
 }
 
+// ------------------------------------------------------- packed FP32 pairs
+// (re, im) or two lanes of FP32 as one 64-bit register pair
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return make_float2(a, b);
+}
+// d += a * b, two FP32 lanes per instruction
+__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
+}
+
 // ---------------------------------------------------------------- stores
 template <int OUT>
 __device__ __forceinline__ void store_out(void* __restrict__ base, long long idx, float2 v) {

@@ -275,6 +275,15 @@ struct RawSrc {
             return (rr < n_raw) ? load_pair_global<IN>(in, rr * C + 2 * cp) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
+    // rows [r0, r0 + n) all inside the stream: load_inside needs no check
+    __device__ __forceinline__ bool inside(int r0, int n) const {
+        if constexpr (RING) return true;
+        else return row0 + r0 + n <= n_raw;
+    }
+    __device__ __forceinline__ float4 load_inside(int r) const {
+        if constexpr (RING) return load(r);
+        else return load_pair_global<IN>(in, (row0 + r) * C + 2 * cp);
+    }
 };
 
 // FIR (Alg. 1) of channel pair cp for the L output spectra whose first raw
@@ -318,21 +327,42 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
         // (slot (i mod L) holds raw row r0+i), T is a runtime loop bound.
         // After tap t the sample r0+t is dead and its slot is refilled with
         // r0+t+L, L taps before it is needed.  Live: L accumulators + L samples.
-        float4 xw[L];
+        // Packed (re, im) x (h, h) FMAs; a segment wholly inside the stream
+        // loads without per-sample bounds checks.
+        unsigned long long ap[L][2];
 #pragma unroll
-        for (int i = 0; i < L; ++i) xw[i] = src.load(r0 + i);
+        for (int j = 0; j < L; ++j) ap[j][0] = ap[j][1] = 0ull;
+        auto run = [&](auto inside_tag) {
+            constexpr bool INSIDE = decltype(inside_tag)::value != 0;
+            auto ld = [&](int r) { return INSIDE ? src.load_inside(r) : src.load(r); };
+            float4 xw[L];
+#pragma unroll
+            for (int i = 0; i < L; ++i) xw[i] = ld(r0 + i);
 #pragma unroll 1
-        for (int tb = 0; tb < T; tb += L) {
+            for (int tb = 0; tb < T; tb += L) {
 #pragma unroll
-            for (int u = 0; u < L; ++u) {
-                const int t = tb + u;
-                if (t < T) {
-                    const float2 h = __ldg(taps2 + t * PAIRS + cp);
+                for (int u = 0; u < L; ++u) {
+                    const int t = tb + u;
+                    if (t < T) {
+                        const float2 h = __ldg(taps2 + t * PAIRS + cp);
+                        const unsigned long long h0 = pk2(h.x, h.x), h1 = pk2(h.y, h.y);
 #pragma unroll
-                    for (int j = 0; j < L; ++j) fma_pair(acc[j], h, xw[(j + u) % L]);
-                    if (t + 1 < T) xw[u] = src.load(r0 + t + L);
+                        for (int j = 0; j < L; ++j) {
+                            const float4 x = xw[(j + u) % L];
+                            ffma2(ap[j][0], h0, pk2(x.x, x.y));
+                            ffma2(ap[j][1], h1, pk2(x.z, x.w));
+                        }
+                        if (t + 1 < T) xw[u] = ld(r0 + t + L);
+                    }
                 }
             }
+        };
+        if (src.inside(r0, L + T - 1)) run(ic<1>{});
+        else run(ic<0>{});
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const float2 a = upk2(ap[j][0]), b = upk2(ap[j][1]);
+            acc[j] = make_float4(a.x, a.y, b.x, b.y);
         }
     }
 }

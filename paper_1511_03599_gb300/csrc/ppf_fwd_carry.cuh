@@ -104,21 +104,6 @@ struct CarryShapeSel {
 template <int C, int TM, int IN>
 struct CarryShape : CarryShapeSel<C, TM, IN>::type {};
 
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return make_float2(a, b);
-}
-// d += a * b, two FP32 lanes per instruction
-__device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long a, unsigned long long b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b));
-}
-
 // FIRONLY: the unfused ablation -- the FIR alone, writing the filtered
 // spectra y (complex FP32, spectrum-major) to global memory instead of
 // transforming them (the paper's FIR kernel followed by a separate DFT).
