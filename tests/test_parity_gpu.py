@@ -132,6 +132,25 @@ def test_batched_shares_cross_streams(ppf, C, T, in_dtype, S, ns):
     assert oracle.rel_l2(y1, oracle.pfb(xs[1], h, C, T)) <= TOL["c64"]
 
 
+@pytest.mark.parametrize("C,T,in_dtype", [(512, 8, "ci8"), (4096, 4, "ci8"), (1536, 8, "cf32")])
+def test_more_streams_than_resident_ctas(ppf, C, T, in_dtype):
+    """400 short streams in one launch: several waves of carry CTAs, or shares of
+    the cluster / generic kernels spanning many streams; bit-identical per stream."""
+    ns, S = 400, 5
+    h = synth.design_taps(C, T)
+    x = np.stack([synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5300 + i) for i in range(ns)])
+    with ppf.Plan(C, T, h, in_dtype, "c64") as plan:
+        yb = plan.execute(to_device(x), n_streams=ns)
+        torch.cuda.synchronize()
+        plan.check_device()
+        for i in (0, 1, 199, 398, 399):
+            yi = plan(to_device(x[i]))
+            torch.cuda.synchronize()
+            assert torch.equal(torch.view_as_real(yb[i]), torch.view_as_real(yi)), f"stream {i}"
+        y = yb[399].cpu().numpy().astype(np.complex128)
+    assert oracle.rel_l2(y, oracle.pfb(x[399], h, C, T)) <= TOL["c64"]
+
+
 @pytest.mark.parametrize("in_dtype", ["ci8", "ci16", "cf32"])
 @pytest.mark.parametrize("out_dtype", ["c64", "c16"])
 @pytest.mark.parametrize("T", [2, 4, 8, 16, 32, 64])
