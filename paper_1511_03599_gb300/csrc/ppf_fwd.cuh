@@ -113,7 +113,9 @@ struct FwdShape {
     static constexpr int PAIRS = C / 2;
     // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k)
     static constexpr int B = (C >= 4096) ? 2 : (C >= 2048) ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
-    static constexpr int L0 = TM >= 32 ? 8 : 16;
+    // large-T FIR order (see fir_segment): tap chunks for narrow input at C <= 512
+    static constexpr bool CHUNK = TM > 16 && IN != IN_CF32 && C <= 512;
+    static constexpr int L0 = (TM >= 32 && !CHUNK) ? 8 : 16;
     static constexpr int L = L0 < B ? L0 : B;                        // FIR segment (outputs)
     static constexpr int G = B / L;                                  // segments per batch
     static constexpr int FIR_ITEMS = PAIRS * G;                      // (pair, segment) items
@@ -291,7 +293,7 @@ struct RawSrc {
 //   acc[j] = sum_{t<T} h[t][cp] * x[r0 + j + t][cp]
 // Every raw sample of the segment (L+T-1 of them) is loaded and converted
 // once; the taps are applied in ascending t for every output.
-template <int TM, int IN, int L, int PAIRS, bool TAPS_IN_REGS, class Src>
+template <int TM, int IN, int L, int PAIRS, bool TAPS_IN_REGS, bool CHUNK, class Src>
 __device__ __forceinline__ void fir_segment(const Src& src, const float2* __restrict__ taps2,
                                             const float2 (&hreg)[TAPS_IN_REGS ? TM : 1], int cp, int r0,
                                             int T, float4 (&acc)[L]) {
@@ -323,36 +325,72 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
             }
         }
     } else {
-        // Large T: tap-outer order with a circular window of L samples
-        // (slot (i mod L) holds raw row r0+i), T is a runtime loop bound.
-        // After tap t the sample r0+t is dead and its slot is refilled with
-        // r0+t+L, L taps before it is needed.  Live: L accumulators + L samples.
-        // Packed (re, im) x (h, h) FMAs; a segment wholly inside the stream
-        // loads without per-sample bounds checks.
+        // Large T (T is a runtime bound); packed (re, im) x (h, h) FMAs; a
+        // segment wholly inside the stream loads without per-sample bounds
+        // checks.  Two orders, chosen per shape by measurement:
+        //  * CHUNK (8/16-bit input, C <= 512): the taps in chunks of K held in
+        //    registers; for each chunk the raw-sample-outer order of the small-T
+        //    path over the L+K-1 rows it needs -- a tap is loaded once per
+        //    segment and serves L outputs (rows are re-read per chunk: cheap
+        //    for narrow samples);
+        //  * otherwise tap-outer with a circular window of L samples (slot
+        //    (i mod L) holds raw row r0+i; after tap t the sample r0+t is dead
+        //    and its slot is refilled with r0+t+L, L taps before it is needed).
+        constexpr int K = 8;
         unsigned long long ap[L][2];
 #pragma unroll
         for (int j = 0; j < L; ++j) ap[j][0] = ap[j][1] = 0ull;
         auto run = [&](auto inside_tag) {
             constexpr bool INSIDE = decltype(inside_tag)::value != 0;
-            auto ld = [&](int r) { return INSIDE ? src.load_inside(r) : src.load(r); };
-            float4 xw[L];
-#pragma unroll
-            for (int i = 0; i < L; ++i) xw[i] = ld(r0 + i);
+            if constexpr (CHUNK) {
 #pragma unroll 1
-            for (int tb = 0; tb < T; tb += L) {
+                for (int tc = 0; tc < T; tc += K) {
+                    unsigned long long h0[K], h1[K];
 #pragma unroll
-                for (int u = 0; u < L; ++u) {
-                    const int t = tb + u;
-                    if (t < T) {
-                        const float2 h = __ldg(taps2 + t * PAIRS + cp);
-                        const unsigned long long h0 = pk2(h.x, h.x), h1 = pk2(h.y, h.y);
+                    for (int tt = 0; tt < K; ++tt) {
+                        const float2 h = (tc + tt < T) ? __ldg(taps2 + (tc + tt) * PAIRS + cp) : make_float2(0.f, 0.f);
+                        h0[tt] = pk2(h.x, h.x);
+                        h1[tt] = pk2(h.y, h.y);
+                    }
 #pragma unroll
-                        for (int j = 0; j < L; ++j) {
-                            const float4 x = xw[(j + u) % L];
-                            ffma2(ap[j][0], h0, pk2(x.x, x.y));
-                            ffma2(ap[j][1], h1, pk2(x.z, x.w));
+                    for (int i = 0; i < L + K - 1; ++i) {
+                        if (tc + i < L + T - 1) {            // rows past the segment's last tap are not needed
+                            const float4 x = INSIDE ? src.load_inside(r0 + tc + i) : src.load(r0 + tc + i);
+                            const unsigned long long x01 = pk2(x.x, x.y), x23 = pk2(x.z, x.w);
+#pragma unroll
+                            for (int j = 0; j < L; ++j) {
+                                const int tt = i - j;
+                                if (tt >= 0 && tt < K) {
+                                    if (IN != IN_CF32 || tc + tt < T) {   // fp32: keep inf/NaN out of unrelated outputs
+                                        ffma2(ap[j][0], h0[tt], x01);
+                                        ffma2(ap[j][1], h1[tt], x23);
+                                    }
+                                }
+                            }
                         }
-                        if (t + 1 < T) xw[u] = ld(r0 + t + L);
+                    }
+                }
+            } else {
+                auto ld = [&](int r) { return INSIDE ? src.load_inside(r) : src.load(r); };
+                float4 xw[L];
+#pragma unroll
+                for (int i = 0; i < L; ++i) xw[i] = ld(r0 + i);
+#pragma unroll 1
+                for (int tb = 0; tb < T; tb += L) {
+#pragma unroll
+                    for (int u = 0; u < L; ++u) {
+                        const int t = tb + u;
+                        if (t < T) {
+                            const float2 h = __ldg(taps2 + t * PAIRS + cp);
+                            const unsigned long long h0 = pk2(h.x, h.x), h1 = pk2(h.y, h.y);
+#pragma unroll
+                            for (int j = 0; j < L; ++j) {
+                                const float4 x = xw[(j + u) % L];
+                                ffma2(ap[j][0], h0, pk2(x.x, x.y));
+                                ffma2(ap[j][1], h1, pk2(x.z, x.w));
+                            }
+                            if (t + 1 < T) xw[u] = ld(r0 + t + L);
+                        }
                     }
                 }
             }
@@ -486,7 +524,7 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
                 src.cp = cp;
             }
             float4 acc[L];
-            fir_segment<TM, IN, L, S::PAIRS, S::TAPS_IN_REGS>(src, taps2, hreg, cp, g * L, T, acc);
+            fir_segment<TM, IN, L, S::PAIRS, S::TAPS_IN_REGS, S::CHUNK>(src, taps2, hreg, cp, g * L, T, acc);
 #pragma unroll
             for (int j = 0; j < L; ++j)
                 *reinterpret_cast<float4*>(ybuf + (g * L + j) * C + 2 * cp) = acc[j];
