@@ -307,23 +307,29 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
             if constexpr (TAPS_IN_REGS) h[t] = hreg[t];
             else h[t] = __ldg(taps2 + t * PAIRS + cp);
         }
+        // a segment wholly inside the stream loads without per-sample bounds checks
+        auto run = [&](auto inside_tag) {
+            constexpr bool INSIDE = decltype(inside_tag)::value != 0;
 #pragma unroll
-        for (int i = 0; i < L + TM - 1; ++i) {
-            if (i < L + T - 1) {
-                const float4 x = src.load(r0 + i);
+            for (int i = 0; i < L + TM - 1; ++i) {
+                if (i < L + T - 1) {
+                    const float4 x = INSIDE ? src.load_inside(r0 + i) : src.load(r0 + i);
 #pragma unroll
-                for (int j = 0; j < L; ++j) {
-                    const int t = i - j;
-                    if (t >= 0 && t < TM) {
-                        if constexpr (IN == IN_CF32) {
-                            if (t < T) fma_pair(acc[j], h[t], x);   // keeps inf/NaN out of unrelated outputs
-                        } else {
-                            fma_pair(acc[j], h[t], x);             // taps t >= T are zero
+                    for (int j = 0; j < L; ++j) {
+                        const int t = i - j;
+                        if (t >= 0 && t < TM) {
+                            if constexpr (IN == IN_CF32) {
+                                if (t < T) fma_pair(acc[j], h[t], x);   // keeps inf/NaN out of unrelated outputs
+                            } else {
+                                fma_pair(acc[j], h[t], x);             // taps t >= T are zero
+                            }
                         }
                     }
                 }
             }
-        }
+        };
+        if (src.inside(r0, L + T - 1)) run(ic<1>{});
+        else run(ic<0>{});
     } else {
         // Large T (T is a runtime bound); packed (re, im) x (h, h) FMAs; a
         // segment wholly inside the stream loads without per-sample bounds
