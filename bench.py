@@ -239,8 +239,8 @@ def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
 def measure_beams(steps: int, dev, seed: int = 4):
     """The multi-beam workload: 96 beams, C in {64..4096}, T in {4, 8, 16},
     spectra per beam uniform in [2^12, 2^17], complex int8 sigma=16 in, complex
-    FP32 out: one persistent launch (C <= 1024 beams) plus one cluster launch per
-    C >= 2048 beam, replayed from a CUDA graph after autotuning."""
+    FP32 out: one persistent launch (C <= 1024 beams) plus one launch per C >= 2048
+    beam of its single-stream kernel, replayed from a CUDA graph after autotuning."""
     import numpy as np
     import torch
     from paper_1511_03599_gb300 import beams, synth
@@ -275,7 +275,7 @@ def measure_beams(steps: int, dev, seed: int = 4):
            "samples": bs.samples(), "ms": ms, "gsps": bs.samples() / ms / 1e6, "GB_s": gbs,
            "hbm_frac": gbs / peak, "tile_samples": tune["tile_samples"], "ctas_per_sm": tune["ctas_per_sm"],
            "launches_per_step": bs.launches_per_execute(), "graph": True, "tiles": bs.info()["tiles"],
-           "cluster_beams": bs.info()["cluster_launches"]}
+           "separate_beam_launches": bs.info()["separate_launches"]}
     bs.close()
     del ins, outs
     return res

@@ -191,12 +191,13 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   persistent kernel (ctas_per_sm CTAs per SM, clamped to what fits; 0 =
  *   most that fit) for the beams with C <= 1024.  Each CTA pulls tiles from
  *   the counter and runs the beam's FIR + DFT for the tile.  Then, on the
- *   same stream, one thread-block-cluster launch per beam with C >= 2048
- *   (the kernel ppf_execute uses for that C).  Every beam's result equals
- *   ppf_execute's.  Asynchronous on `stream`; no allocation.
+ *   same stream, one launch per beam with C >= 2048 of the single-stream
+ *   kernel ppf_execute uses for that shape (thread-block cluster or generic).
+ *   Every beam's result equals ppf_execute's.  Asynchronous on `stream`; no
+ *   allocation.
  * ppf_beams_info -- info[0]=beams, [1]=tiles (of the persistent launch),
  *   [2]=tile samples, [3]=max CTAs per SM, [4]=SMs, [5]=dynamic shared memory
- *   bytes, [6]=cluster launches (beams with C >= 2048).
+ *   bytes, [6]=separate launches (beams with C >= 2048).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
  * ppf_beams_destroy -- free everything (NULL accepted).
  * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY, DEVICE_TIMEOUT.

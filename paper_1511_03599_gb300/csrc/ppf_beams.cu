@@ -8,11 +8,12 @@
 // can be captured in a CUDA graph), reads the tile's beam descriptor and runs
 // the FIR + DFT of that range with the code of the beam's (C, tap bucket)
 // class.  All classes share one block size (256 threads) and one dynamic
-// shared-memory size (the largest class's).  Beams with C >= 2048 whose state
-// does not fit one SM instead run, after the persistent launch and on the same
-// stream, one thread-block-cluster launch each (the single-stream kernel of
-// ppf_execute).  Complex int8 input, complex FP32 output: the multi-beam
-// workload of the channeliser.
+// shared-memory size (the largest class's).  Beams with C >= 2048 instead
+// run, after the persistent launch and on the same stream, one launch each of
+// the single-stream kernel ppf_execute uses for their shape (a thread-block
+// cluster kernel or the generic one, with the grid the GPU holds at once).
+// Complex int8 input, complex FP32 output: the multi-beam workload of the
+// channeliser.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -140,13 +141,12 @@ ppf_status bcuda(cudaError_t e, const char* what) {
 
 constexpr uint32_t kBeamsMagic = 0x50504642u;   // "PPFB"
 
-// The cluster kernel entry for a beam, if the beam runs on one.
-bool cluster_entry(int C, int T, ppf::FwdEntry* e) {
+// The single-stream kernel of a beam that runs on its own launch (C >= 2048).
+bool separate_entry(int C, int T, ppf::FwdEntry* e) {
     const int tm = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16;
-    bool ok = false;
-    if (C == 2048) ok = ppf::fwd_lookup_c2048(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
-    else if (C == 4096) ok = ppf::fwd_lookup_c4096(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
-    return ok && e->cluster > 0;
+    if (C == 2048) return ppf::fwd_lookup_c2048(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
+    if (C == 4096) return ppf::fwd_lookup_c4096(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
+    return false;
 }
 
 int class_of(int C, int T) {
@@ -166,9 +166,9 @@ struct ppf_beams_s {
     long long tile_samples;
     std::vector<ppf::BeamDesc> host;       // descriptors (pointers bound by ppf_beams_bind)
     std::vector<int> tm;                   // tap bucket per beam
-    std::vector<int> big;                  // beams run by a cluster launch each
+    std::vector<int> big;                  // beams run by a launch of their own
     std::vector<ppf::FwdEntry> big_entry;  // their kernels
-    std::vector<int> big_clusters;         // resident clusters of each
+    std::vector<int> big_units;            // resident work units (CTAs or clusters) of each
     ppf::BeamDesc* d_beams;
     ppf::BeamTile* d_tiles;
     long long n_tiles;
@@ -315,19 +315,26 @@ extern "C" ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C
         b->host[i].taps = b->d_taps + taps_off[i];
         b->host[i].tw = b->d_tw + tw_off[C[i]];
         ppf::FwdEntry e{};
-        if (!cluster_entry(C[i], T[i], &e)) continue;
-        int clusters = 0;
+        if (!separate_entry(C[i], T[i], &e)) continue;
+        int units = 0;
         ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem);
-        if (ce == cudaSuccess) ce = ppf::max_active_clusters(e, sms, &clusters);
+        if (ce == cudaSuccess) {
+            if (e.cluster > 0) {
+                ce = ppf::max_active_clusters(e, sms, &units);
+            } else {
+                ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&units, e.fn, e.threads, e.smem);
+                units *= sms;
+            }
+        }
         if (ce != cudaSuccess) {
-            ppf_status s = bcuda(ce, "ppf_beams_plan: cluster kernel");
+            ppf_status s = bcuda(ce, "ppf_beams_plan: single-beam kernel");
             ppf_beams_destroy(b);
             return s;
         }
-        if (clusters < 1) continue;   // stays on the persistent kernel
+        if (units < 1) continue;      // stays on the persistent kernel
         b->big.push_back(i);
         b->big_entry.push_back(e);
-        b->big_clusters.push_back(clusters);
+        b->big_units.push_back(units);
     }
     ppf_status s = build_tiles(b, 1ll << 20);
     if (s != PPF_OK) {
@@ -387,15 +394,16 @@ extern "C" ppf_status ppf_beams_execute(ppf_beams_t b, int ctas_per_sm, ppf_stre
         fa.out_stride = 0;
         const long long nb = (d.n_spectra + e.batch - 1) / e.batch;
         fa.n_streams = 1;
-        const long long clusters = std::min<long long>(b->big_clusters[j], nb);
+        const long long units = std::min<long long>(b->big_units[j], nb);
+        const int per_unit = e.cluster > 0 ? e.cluster : 1;
         fa.taps = d.taps;
         fa.tw = d.tw;
         fa.err = b->d_err;
         fa.n_spectra = d.n_spectra;
         fa.T = d.T;
         fa.flags = 0;
-        ce = e.launch(fa, (int)(clusters * e.cluster), st);
-        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: cluster launch");
+        ce = e.launch(fa, (int)(units * per_unit), st);
+        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: single-beam launch");
     }
     return PPF_OK;
 }

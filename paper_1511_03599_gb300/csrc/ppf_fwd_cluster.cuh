@@ -1,5 +1,7 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
-// (C = 2048, 3072, 4096, and most C = 768 shapes) on a thread-block cluster.
+// on a thread-block cluster (used where it measured faster than the
+// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input at C = 4096;
+// C = 3072 is supported as well).
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
@@ -60,9 +62,11 @@ struct ClusterShape {
     static constexpr int TW_OFF = 3 * YLB;
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
-    // where it measured faster than the single-CTA kernels: C >= 2048, and
-    // C = 768 except 8-tap int8 (C = 1024 fp32 and C = 1536 were slower)
-    static constexpr bool WANTED = C >= 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8));
+    // where it measured faster than the single-CTA kernels: C = 2048, C = 768
+    // except 8-tap int8, and fp32 input at C = 4096 (the generic kernel won
+    // at C = 3072, at C = 4096 for 8/16-bit input, at C = 1024 and 1536)
+    static constexpr bool WANTED = C == 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
+                                   (C == 4096 && IN == IN_CF32);
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
 };

@@ -101,16 +101,16 @@ def test_beams_reject_unsupported(mods):
         beams.BeamSet([512], [32], [10], [synth.design_taps(512, 32)])
 
 
-def test_beams_large_channel_counts_use_cluster_launches(mods):
-    """C >= 2048 beams run the single-stream cluster kernel: bit-identical to ppf_execute,
-    one launch each; a set of only such beams has no persistent launch at all."""
+def test_beams_large_channel_counts_use_separate_launches(mods):
+    """C >= 2048 beams run the single-stream kernel of their shape: bit-identical to
+    ppf_execute, one launch each; a set of only such beams has no persistent launch."""
     ppf, _ = mods
     for beams_def in ([(2048, 8, 300), (4096, 4, 100), (512, 8, 200), (2048, 16, 57)],
                       [(2048, 3, 129), (4096, 16, 64)]):
         bs, xs, taps, ins, outs = make_set(mods, beams_def, seed=120)
         n_big = sum(1 for c, _, _ in beams_def if c >= 2048)
         info = bs.info()
-        assert info["cluster_launches"] == n_big
+        assert info["separate_launches"] == n_big
         assert bs.launches_per_execute() == n_big + (1 if info["tiles"] > 0 else 0)
         assert (info["tiles"] > 0) == any(c < 2048 for c, _, _ in beams_def)
         bs.execute()

@@ -74,9 +74,10 @@ def test_parity_non_power_of_two_channels(ppf, C, T, in_dtype, out_dtype):
     run_case(ppf, C, T, S, in_dtype, out_dtype, seed=4000 + C + T)
 
 
-# C >= 2048: a thread-block cluster shares each stream (one 512-channel slice
-# per CTA, the first DFT stage gathered across the cluster).  Enough spectra
-# that every cluster carries its FIR state over several batches.
+# Large C: the thread-block-cluster kernel (a slice of channels per CTA, the
+# first DFT stage gathered across the cluster) where the plan picks it, else
+# the generic kernel.  Enough spectra that every work unit carries its FIR
+# state over several batches.
 @pytest.mark.parametrize("C", [768, 1024, 1536, 2048, 3072, 4096])
 @pytest.mark.parametrize("T,in_dtype,out_dtype", [(8, "ci8", "c64"), (4, "cf32", "c64"), (16, "ci16", "c16"),
                                                   (1, "ci8", "c64"), (13, "ci8", "c64"), (2, "cf32", "c16")])
