@@ -1,7 +1,6 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
 // on a thread-block cluster (used where it measured faster than the
-// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input at C = 4096;
-// C = 3072 is supported as well).
+// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input at C = 4096).
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
