@@ -482,6 +482,7 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
         }
         __syncthreads();
         if (tid == 0) {
+            fence_proxy_async_smem();   // the slots were last read by the previous range's FIR
             for (; issued < NS && issued <= last_needed; ++issued) issue(issued);
         }
     }
@@ -548,6 +549,12 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
         static_for<NST>([&](auto p) {
             fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, out, sb, 0, n_spectra);
         });
+    }
+    if constexpr (RING) {
+        // every copy of the range has landed (thread 0 waited for each):
+        // retire the barriers, the next range of this CTA initialises them anew
+        if (tid == 0)
+            for (int i = 0; i <= NS; ++i) mbar_inval(&bars[i]);
     }
     return true;
 }

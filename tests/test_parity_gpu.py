@@ -133,10 +133,12 @@ def test_batched_shares_cross_streams(ppf, C, T, in_dtype, S, ns):
     assert oracle.rel_l2(y1, oracle.pfb(xs[1], h, C, T)) <= TOL["c64"]
 
 
-@pytest.mark.parametrize("C,T,in_dtype", [(512, 8, "ci8"), (4096, 4, "ci8"), (1536, 8, "cf32")])
+@pytest.mark.parametrize("C,T,in_dtype", [(512, 8, "ci8"), (4096, 4, "ci8"), (1536, 8, "cf32"),
+                                          (384, 8, "ci8"), (32, 4, "ci8"), (4096, 2, "ci8")])
 def test_more_streams_than_resident_ctas(ppf, C, T, in_dtype):
     """400 short streams in one launch: several waves of carry CTAs, or shares of
-    the cluster / generic kernels spanning many streams; bit-identical per stream."""
+    the cluster / generic kernels spanning many streams (the generic kernel in its
+    TMA-ring mode at C=384, 32 and 4096 with T <= 2); bit-identical per stream."""
     ns, S = 400, 5
     h = synth.design_taps(C, T)
     x = np.stack([synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5300 + i) for i in range(ns)])
