@@ -259,7 +259,9 @@ const char* ppf_last_error_message(void);
  *   (CTAs), info[3]=dynamic shared memory bytes, info[4]=tap bucket (T
  *   rounded up), info[5]=number of FFT stages, info[6]=kernel variant
  *   (bit 0: raw input staged through a TMA ring in shared memory; bit 1:
- *   twiddles in shared memory), info[7]=CTAs resident per SM. */
+ *   twiddles in shared memory; bit 2: FIR halo carried in registers between
+ *   batches; bit 4: thread-block-cluster kernel, info[2] then counts the
+ *   CTAs of whole clusters), info[7]=CTAs resident per SM. */
 ppf_status ppf_plan_info(ppf_plan_t plan, int info[8]);
 
 /*
