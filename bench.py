@@ -11,9 +11,18 @@ Prints ONE JSON line (rank 0).  ``value`` is input GSamples/s over all ranks
 (C * spectra / time, the sample rate f_s of Sec. 3); ``roofline`` relates the
 kernel's algorithmic bytes to the measured HBM copy bandwidth; ``e2e`` is the
 same metric through the host-buffer entry point (copies included);
-``cpu_baseline`` is the FP64 oracle on a bounded sample on the host cores.
+``cpu_baseline`` is the FP64 oracle on a bounded sample of the same input on
+the host cores, with the GPU output's error against it.  Beside the headline:
+``precision`` (the same shape with fp32 and int16 input, each with its own
+roofline), ``sweep`` (C=512, T in {8,16,32,64} x {int16, fp32} in x
+{complex64, complex FP16} out, 2^18 spectra, against min(HBM, FP32) roofs),
+``large_c`` (C=2048 and 4096), ``fwd_bwd``, ``batched_beams`` and the unfused
+ablation.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 outside torchrun, the script launches N ranks of itself
+through torch.distributed.run (one process per GPU, rendezvous on 127.0.0.1).
 """
 from __future__ import annotations
 
@@ -48,6 +57,9 @@ def parse():
     ap.add_argument("--no-fwd-bwd", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-beams", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-large-c", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)   # internal: one timed oracle run
     return ap.parse_args()
@@ -154,6 +166,71 @@ class ClockSampler:
 def kernel_name(w, info):
     name = "pfb_fwd_carry_kernel" if info["variant"] & 4 else "pfb_fwd_kernel"
     return f"{name}<{w.C},{info['tap_bucket']},{w.in_dtype},{w.out_dtype}>"
+
+
+def fp32_peak_flops(dev, sm_mhz=None):
+    """FP32 CUDA-core peak: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz
+    if not mhz:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = float(json.load(f)["sm_max_mhz"])
+        except Exception:
+            mhz = 2070.0
+    return sms * 128 * 2 * mhz * 1e6
+
+
+def flops_per_sample(C: int, T: int) -> float:
+    """Algorithmic FP32 work per input sample: the FIR's 2(2T-1) (Sec. 4.1) plus
+    the radix-2 FFT count 5 log2 C (3 * 2^k: the same formula, as a reference)."""
+    import math
+    return 2 * (2 * T - 1) + 5 * math.log2(C)
+
+
+def time_launches(fn, steps: int, warmup: int, stream) -> float:
+    """Mean ms per call of fn over `steps` calls, CUDA events on `stream`, after warm-up."""
+    import torch
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def measure_case(w, steps: int, warmup: int, dev, peak: float, fp32_peak: float) -> dict:
+    """One forward workload: kernel time (CUDA events), input GS/s, its own
+    roofline (algorithmic bytes / time against the HBM copy peak) and, for the
+    FP32 co-bound, the fraction of min(HBM roof, FP32 roof) in samples/s."""
+    import torch
+    from paper_1511_03599_gb300 import ppf, synth
+    x = synth.stream_torch(w.C, w.n_raw, w.in_dtype, w.sigma, w.seed, w.tones, device=dev)
+    st = torch.cuda.current_stream()
+    with ppf.Plan(w.C, w.T, w.taps(), w.in_dtype, w.out_dtype) as plan:
+        y = plan.empty_output(w.S, device=dev)
+        ms = time_launches(lambda: plan.execute(x, out=y, stream=st), steps, warmup, st)
+        plan.check_device()
+        info = plan.info()
+        finite = bool(torch.isfinite(y.float() if w.out_dtype == "c16" else torch.view_as_real(y)).all())
+    b_in, b_out = synth.in_bytes_per_sample(w.in_dtype), synth.out_bytes_per_sample(w.out_dtype)
+    alg = w.C * w.n_raw * b_in + w.C * w.S * b_out + 4 * w.C * w.T
+    gsps = w.C * w.S / ms / 1e6
+    achieved = alg / ms / 1e6
+    hbm_roof = peak * 1e9 / (alg / (w.C * w.S)) / 1e9
+    fp_roof = fp32_peak / flops_per_sample(w.C, w.T) / 1e9
+    del x, y
+    return {"workload": w.name, "C": w.C, "T": w.T, "spectra": w.S, "in": w.in_dtype, "out": w.out_dtype,
+            "ms": ms, "gsps": gsps, "all_outputs_finite": finite,
+            "roofline": {"bound": "hbm" if hbm_roof <= fp_roof else "fp32", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "algorithmic_bytes_per_launch": alg},
+            "hbm_roof_gsps": hbm_roof, "fp32_roof_gsps": fp_roof,
+            "frac_of_min_roof": gsps / min(hbm_roof, fp_roof), "launch": info}
 
 
 def measure_fwd_bwd(steps: int, warmup: int, dev):
@@ -281,8 +358,14 @@ def measure_beams(steps: int, dev, seed: int = 4):
     return res
 
 
-def cpu_baseline(w, target_s: float):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(w, target_s: float, x_dev=None, y_dev=None):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload.
+
+    With the benchmark's device input and output given, the sample is the
+    first S spectra of that very input (copied to the host), and the GPU
+    output of the timed run is compared with the oracle's on those spectra and
+    on the last 2T spectra of the stream: whole-sample relative L2 and the
+    per-spectrum maximum of the same ratio."""
     import numpy as np
 
     import oracle
@@ -290,20 +373,43 @@ def cpu_baseline(w, target_s: float):
 
     h = w.taps()
 
+    def sample_input(S):
+        if x_dev is None:
+            return synth.stream(w.C, S + w.T - 1, w.in_dtype, w.sigma, w.seed, w.tones)
+        return x_dev[: (S + w.T - 1) * w.C].cpu().numpy()
+
     def run(S):
-        x = synth.stream(w.C, S + w.T - 1, w.in_dtype, w.sigma, w.seed, w.tones)
+        x = sample_input(S)
         t0 = time.perf_counter()
-        oracle.pfb(x, h, w.C, w.T)
-        return time.perf_counter() - t0
+        Y = oracle.pfb(x, h, w.C, w.T)
+        return time.perf_counter() - t0, Y
 
     S = 256
-    dt = run(S)
+    dt, _ = run(S)
     S = int(max(256, min(w.S, S * target_s / max(dt, 1e-3))))
-    dt = run(S)
+    dt, Y = run(S)
     cores = os.cpu_count()
     res = {"value": w.C * S / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"{S} of {w.S} spectra of {w.name} (FP64 direct FIR + naive O(C^2) DFT, numpy)",
            "seconds": dt}
+    if y_dev is not None:
+        def as_np(y):
+            if w.out_dtype == "c64":
+                return y.cpu().numpy().astype(np.complex128)
+            a = y.float().cpu().numpy()
+            return a[..., 0].astype(np.float64) + 1j * a[..., 1]
+        got = as_np(y_dev[:S])
+        n_tail = min(w.S, 2 * w.T)
+        s0 = w.S - n_tail
+        xt = x_dev[s0 * w.C:].cpu().numpy()
+        Yt = oracle.pfb(xt, h, w.C, w.T)
+        gt = as_np(y_dev[s0:])
+        res["parity"] = {"spectra_compared": S + n_tail,
+                         "rel_l2": oracle.rel_l2(np.concatenate([got, gt]), np.concatenate([Y, Yt])),
+                         "max_per_spectrum_rel_l2": max(oracle.rel_l2_max_per_spectrum(got, Y),
+                                                        oracle.rel_l2_max_per_spectrum(gt, Yt)),
+                         "tolerance": 1e-5 if w.out_dtype == "c64" else 2e-3,
+                         "compared": f"first {S} and last {n_tail} output spectra of the timed run"}
     # the same oracle on one core: a child process with every BLAS / OpenMP pool at one thread
     try:
         s1 = max(64, S // max(1, cores) // 2)
@@ -382,7 +488,8 @@ def run_reference(args, w):
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     v = w.C * S / t / 1e9
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(w.describe(), sample_spectra_per_step=S),
@@ -392,8 +499,25 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def free_port() -> int:
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def relaunch_command(n: int, argv, port: int):
+    """torch.distributed.run command that starts n ranks of this script (one per GPU)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.oracle_sample == 0:
+        # one process per GPU: launch the ranks, wait for them, pass their status on
+        r = subprocess.run(relaunch_command(args.gpus, sys.argv[1:], free_port()))
+        sys.exit(r.returncode)
     from paper_1511_03599_gb300 import synth
     w = synth.target_workload(args.in_dtype, args.spectra)
     if args.oracle_sample > 0:
@@ -409,6 +533,8 @@ def main():
 
     from paper_1511_03599_gb300 import dist as pdist
     rank, local, world = pdist.env_rank_world()
+    if world != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but {world} rank(s) were launched")
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -520,18 +646,55 @@ def main():
         fb = measure_fwd_bwd(max(5, args.steps), args.warmup, dev)
         try:
             from paper_1511_03599_gb300 import fit
-            r = fit.fit_taps(steps=20)
-            fb["tap_fit"] = {"optimizer": "Adam lr=1e-3", "steps": 20, "leakage_first": r["loss"][0],
-                             "leakage_last": r["loss"][-1], "leakage_sinc_hamming": r["sinc_hamming_loss"],
-                             "ms_per_step": r["ms_per_step"],
-                             "loss": "out-of-band energy of a per-stream off-centre tone set"}
+            r = fit.fit_taps()
+            fb["tap_fit"] = {k: r[k] for k in ("optimizer", "steps", "ms_per_step", "phase_ms", "sinc_hamming_loss")}
+            fb["tap_fit"].update({"leakage_first": r["loss"][0], "leakage_last": r["loss"][-1],
+                                  "loss": "out-of-band energy of a per-stream off-centre tone set"})
         except Exception as e:  # noqa: BLE001 - context beside the metric
             fb["tap_fit"] = {"error": str(e)}
+
+    # the same shape with fp32 and int16 input, the tap/precision sweep (C=512,
+    # 2^18 spectra) and large channel counts: kernel time of each, own roofline
+    fp32_peak = fp32_peak_flops(dev, clk.summary().get("sm_mhz"))
+    cell_steps = max(5, args.steps // 2)
+    prec = None
+    if not args.no_precision:
+        prec = {}
+        for d in ("cf32", "ci16"):
+            if d != w.in_dtype:
+                try:
+                    prec[d] = measure_case(synth.target_workload(d, args.spectra), cell_steps, args.warmup, dev,
+                                           peak, fp32_peak)
+                except Exception as e:  # noqa: BLE001 - reported beside the metric
+                    prec[d] = {"error": str(e)}
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        for T in (8, 16, 32, 64):
+            for d in ("ci16", "cf32"):
+                for o in ("c64", "c16"):
+                    try:
+                        sweep.append(measure_case(synth.sweep_workload(T, d, o), cell_steps, args.warmup, dev,
+                                                  peak, fp32_peak))
+                    except Exception as e:  # noqa: BLE001
+                        sweep.append({"workload": f"T={T} {d}->{o}", "error": str(e)})
+    large = None
+    if not args.no_large_c:
+        large = []
+        for C in (1024, 2048, 4096):
+            try:
+                lw = synth.Workload(f"pfb_c{C}_t8_s{(1 << 28) // C}_ci8_c64", C, 8, (1 << 28) // C, "ci8", "c64",
+                                    16.0, synth.SEED_BASE + 30 + C, ())
+                large.append(measure_case(lw, cell_steps, args.warmup, dev, peak, fp32_peak))
+            except Exception as e:  # noqa: BLE001
+                large.append({"workload": f"C={C}", "error": str(e)})
 
     if rank == 0:
         cpu = cpu_f = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = cpu_baseline(w, args.cpu_seconds)
+            plan.execute(x, out=y, stream=stream)     # y holds the fused result again (the ablation overwrote it)
+            torch.cuda.synchronize()
+            cpu = cpu_baseline(w, args.cpu_seconds, x, y)
             try:
                 cpu_f = cpu_fast(w, min(5.0, args.cpu_seconds))
             except Exception as e:  # noqa: BLE001 - context beside the metric
@@ -557,6 +720,9 @@ def main():
             "fwd_bwd": fb,
             "unfused_ablation": abl,
             "batched_beams": bm,
+            "precision": prec,
+            "sweep": sweep,
+            "large_c": large,
             "cpu_baseline": cpu,
             "cpu_fast": cpu_f,
             "wall_s_timed": wall,

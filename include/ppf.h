@@ -132,6 +132,10 @@ ppf_status ppf_execute_batched(ppf_plan_t plan, const void* in_dev, long long in
  * (per-CTA partial sums, then a fixed-order sum); the partial-sum scratch is
  * allocated by the plan on the first call and grown when a call needs more
  * CTAs (cudaMalloc inside the call).  Asynchronous on `stream`.
+ * If a bounded device wait gives up (ppf_check_device then reports
+ * PPF_ERR_DEVICE_TIMEOUT), grad_in is incomplete and every element of
+ * grad_taps is NaN; the plan's status word stays set until ppf_check_device
+ * clears it, and tap gradients computed meanwhile are NaN too.
  * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY.
  */
 ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
@@ -261,7 +265,10 @@ const char* ppf_last_error_message(void);
  *   (bit 0: raw input staged through a TMA ring in shared memory; bit 1:
  *   twiddles in shared memory; bit 2: FIR halo carried in registers between
  *   batches; bit 4: thread-block-cluster kernel, info[2] then counts the
- *   CTAs of whole clusters), info[7]=CTAs resident per SM. */
+ *   CTAs of whole clusters; bit 5: the cluster's CTAs push their filtered
+ *   channels into the transforming CTA's shared memory; bit 6: long-tap
+ *   kernel, T = 17..64, raw rows and halo streamed through a TMA ring),
+ *   info[7]=CTAs resident per SM. */
 ppf_status ppf_plan_info(ppf_plan_t plan, int info[8]);
 
 /*

@@ -153,6 +153,26 @@ def efficiency(S: int, T: int) -> float:
     return S / (S + T - 1)
 
 
+def rel_l2_max_per_spectrum(a: np.ndarray, ref: np.ndarray) -> float:
+    """max over spectra s of ||a[s] - ref[s]||_2 / ||ref[s]||_2, in FP64.
+
+    ``a`` and ``ref`` have shape (..., C) (the last axis is the bins of one
+    spectrum).  A spectrum whose reference is all zero contributes its
+    absolute error norm.
+    """
+    a = np.asarray(a).astype(np.complex128)
+    ref = np.asarray(ref).astype(np.complex128)
+    if a.shape != ref.shape or a.ndim < 1:
+        raise ValueError("a and ref must have the same shape (..., C)")
+    if a.size == 0:
+        return 0.0
+    C = ref.shape[-1]
+    num = np.linalg.norm((a - ref).reshape(-1, C), axis=1)
+    den = np.linalg.norm(ref.reshape(-1, C), axis=1)
+    r = np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+    return float(np.max(r))
+
+
 def rel_l2(a: np.ndarray, ref: np.ndarray) -> float:
     """||a - ref||_2 / ||ref||_2 over all elements, evaluated in FP64."""
     a = np.asarray(a).astype(np.complex128).ravel()

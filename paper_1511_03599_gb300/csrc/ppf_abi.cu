@@ -404,7 +404,7 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
     cudaError_t ce = p->bwd.launch(a, (int)grid, st);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: launch");
     if (grad_taps_dev != nullptr) {
-        ce = ppf::bwd_reduce(p->d_partials, (int)grid, T, TM, C, grad_taps_dev, st);
+        ce = ppf::bwd_reduce(p->d_partials, (int)grid, T, TM, C, p->d_err, grad_taps_dev, st);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: tap-gradient reduction");
     }
     return PPF_OK;
@@ -616,7 +616,7 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     cudaError_t ce = p->bwd.launch(a, (int)grid, cs);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: launch");
     if (grad_taps_dev != nullptr) {
-        ce = ppf::bwd_reduce(partials, (int)grid, T, TM, C, grad_taps_dev, cs);
+        ce = ppf::bwd_reduce(partials, (int)grid, T, TM, C, p->d_err, grad_taps_dev, cs);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward_noalloc: tap-gradient reduction");
     }
     return PPF_OK;

@@ -34,9 +34,10 @@ bool bwd_lookup(int C, int tm, BwdEntry* e) {
     }
 }
 
-cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, float* grad_h, cudaStream_t st) {
+cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, const int* err, float* grad_h,
+                       cudaStream_t st) {
     const int TC = T * C;
-    pfb_bwd_reduce_kernel<<<(TC + 255) / 256, 256, 0, st>>>(partials, nparts, TC, TM * C, grad_h);
+    pfb_bwd_reduce_kernel<<<(TC + 255) / 256, 256, 0, st>>>(partials, nparts, TC, TM * C, err, grad_h);
     return cudaPeekAtLastError();
 }
 

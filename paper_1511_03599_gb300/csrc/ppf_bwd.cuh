@@ -258,11 +258,17 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
     }
 }
 
-// grad_h[t*C + c] = sum over CTAs, in CTA order, of the partial sums.
+// grad_h[t*C + c] = sum over CTAs, in CTA order, of the partial sums.  When
+// the status word is set (a bounded wait of the adjoint gave up, so some
+// partial rows were never written), every element is NaN instead.
 static __global__ void pfb_bwd_reduce_kernel(const float* __restrict__ partials, int nparts, int TC, int TMC,
-                                      float* __restrict__ grad_h) {
+                                      const int* __restrict__ err, float* __restrict__ grad_h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= TC) return;
+    if (*err != 0) {
+        grad_h[i] = __int_as_float(0x7fc00000);
+        return;
+    }
     float s = 0.f;
     for (int p = 0; p < nparts; ++p) s += partials[(size_t)p * TMC + i];
     grad_h[i] = s;

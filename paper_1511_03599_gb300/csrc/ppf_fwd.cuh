@@ -98,13 +98,27 @@ __device__ __forceinline__ int phys(int i) {
         return i;
     }
 }
-// Twiddle table offsets: stage p (p < P-1) holds W_{N_p}^{b k} at [k*N_{p+1} + b].
+// Twiddle tables: stage p (p < P-1) holds W_{N_p}^{b k}, k = 1 .. R_p-1, for
+// the N_{p+1} columns b: (R_p - 1) * N_{p+1} entries at [(k-1)*N_{p+1} + b],
+// so lanes with consecutive b read consecutive entries.  (A layout with the
+// entries of one column adjacent, read as 16-byte (k, k+1) pairs, measured
+// slower at C = 512.)
 constexpr int tw_offset(int C, int p) {
     int off = 0;
-    for (int q = 0; q < p; ++q) off += fft_n(C, q);
+    for (int q = 0; q < p; ++q) off += (fft_n(C, q) / fft_radix(C, q)) * (fft_radix(C, q) - 1);
     return off;
 }
 constexpr int tw_size(int C) { return tw_offset(C, fft_stages(C) - 1); }
+
+// v[k] *= W_{N_p}^{b k} for k = 1 .. R-1; tw_stage is stage p's table (NN = N_{p+1} columns)
+template <int R, int NN, bool TW_SMEM>
+__device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __restrict__ tw_stage, int b) {
+#pragma unroll
+    for (int k = 1; k < R; ++k) {
+        const float2* p = tw_stage + (k - 1) * NN + b;
+        v[k] = cmul(v[k], TW_SMEM ? *p : __ldg(p));
+    }
+}
 
 // ------------------------------------------------------------ launch shape
 template <int C, int TM, int IN, int NTO = 0>
@@ -215,12 +229,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         const int b = e % NN, prefix = e / NN;
         dft_reg<R>(v[it]);
         if constexpr (P + 1 < NST) {
-            const float2* twp = tws + tw_offset(C, P);
-#pragma unroll
-            for (int k = 1; k < R; ++k) {
-                const float2 w = TW_SMEM ? twp[k * NN + b] : __ldg(twp + k * NN + b);
-                v[it][k] = cmul(v[it][k], w);
-            }
+            apply_twiddles<R, NN, TW_SMEM>(v[it], tws + tw_offset(C, P), b);
             float2* dst = ybuf + sp * SPAN;
 #pragma unroll
             for (int k = 0; k < R; ++k) dst[phys<C, P + 1, LAYOUT>((prefix + PP * k) * NN + b)] = v[it][k];
@@ -604,6 +613,19 @@ struct FwdInfo {
 
 #include "ppf_fwd_carry.cuh"
 #include "ppf_fwd_cluster.cuh"
+#include "ppf_fwd_push.cuh"
+#include "ppf_fwd_longtap.cuh"
+
+// Selection switches for the push-exchange cluster kernel (C = 2048/4096,
+// int8) and the long-tap kernel (T = 17..64, C <= 512): both pass every
+// parity test but measured slower than the generic and cluster kernels they
+// would replace, so they are compiled only when enabled.
+#ifndef PPF_NO_PUSH
+#define PPF_NO_PUSH 1
+#endif
+#ifndef PPF_NO_LONGTAP
+#define PPF_NO_LONGTAP 1
+#endif
 
 namespace ppf {
 
@@ -613,10 +635,18 @@ inline FwdInfo fwd_info() {
         using S = CarryShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4,
                        reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT>), 0};
+    } else if constexpr (PushShape<C, TM, IN>::OK && !PPF_NO_PUSH) {
+        using S = PushShape<C, TM, IN>;
+        return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | 2 | 4 | 16 | 32,
+                       reinterpret_cast<const void*>(&pfb_fwd_push_kernel<C, TM, IN, OUT>), S::Q};
     } else if constexpr (ClusterShape<C, TM, IN>::OK) {
         using S = ClusterShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4 | 16,
                        reinterpret_cast<const void*>(&pfb_fwd_cluster_kernel<C, TM, IN, OUT>), S::Q};
+    } else if constexpr (TM == 64 && LongShape<C, IN>::OK && !PPF_NO_LONGTAP) {
+        using S = LongShape<C, IN>;
+        return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | 2 | 64,
+                       reinterpret_cast<const void*>(&pfb_fwd_longtap_kernel<C, IN, OUT>), 0};
     } else {
         using S = FwdShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, (S::RING ? 1 : 0) | (S::TW_SMEM ? 2 : 0),
@@ -630,9 +660,15 @@ inline cudaError_t fwd_launch(const FwdArgs& a, int grid, cudaStream_t st) {
     if constexpr (CarryShape<C, TM, IN>::OK) {
         using S = CarryShape<C, TM, IN>;
         pfb_fwd_carry_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    } else if constexpr (PushShape<C, TM, IN>::OK && !PPF_NO_PUSH) {
+        using S = PushShape<C, TM, IN>;
+        pfb_fwd_push_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
     } else if constexpr (ClusterShape<C, TM, IN>::OK) {
         using S = ClusterShape<C, TM, IN>;
         pfb_fwd_cluster_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
+    } else if constexpr (TM == 64 && LongShape<C, IN>::OK && !PPF_NO_LONGTAP) {
+        using S = LongShape<C, IN>;
+        pfb_fwd_longtap_kernel<C, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
     } else {
         using S = FwdShape<C, TM, IN>;
         pfb_fwd_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
@@ -665,15 +701,16 @@ inline cudaError_t fir_launch(const FwdArgs& a, int grid, cudaStream_t st) {
 }
 
 // Twiddle table contents (host, FP64 -> FP32): stage p < P-1 holds
-// W_{N_p}^{b k} = exp(-2 pi i b k / N_p) at [tw_offset(p) + k*N_{p+1} + b].
+// W_{N_p}^{b k} = exp(-2 pi i b k / N_p), k = 1 .. R_p-1, at
+// [tw_offset(p) + (k-1)*N_{p+1} + b].
 template <int C>
 inline void fill_twiddles(float2* host) {
     for (int p = 0; p + 1 < fft_stages(C); ++p) {
         const int NP = fft_n(C, p), R = fft_radix(C, p), NN = NP / R;
-        for (int k = 0; k < R; ++k)
+        for (int k = 1; k < R; ++k)
             for (int b = 0; b < NN; ++b) {
                 const long e = (long)b * k % NP;
-                host[tw_offset(C, p) + k * NN + b] =
+                host[tw_offset(C, p) + (k - 1) * NN + b] =
                     make_float2((float)cos2pi(e, NP), (float)(-sin2pi(e, NP)));
             }
     }

@@ -10,7 +10,11 @@
 // by one thread once, and the copy of batch k+1 has a whole batch of compute
 // (FIR k and the FFT of k) to land.  Because of the carry, batch k produces
 // output spectra (lo+k)B - (T-1) .. (lo+k)B + B - T; the CTA processes
-// nb + 1 raw batches and stores only the outputs of its own range.
+// nb + 1 raw batches and stores only the outputs of its own range.  (Slots
+// shifted by T-1 rows, so that no halo-only batch is needed, measured 1.4 %
+// slower at C = 512, T = 8, int8; a loop unrolled by two batches that
+// alternates two register sets for the carried rows instead of copying them
+// spilled registers.)
 //
 // The FIR uses packed FP32 pairs (fma.rn.f32x2): (re, im) of a sample times
 // its (h, h) tap in one instruction.

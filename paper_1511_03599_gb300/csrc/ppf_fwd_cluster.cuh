@@ -129,11 +129,8 @@ __device__ __forceinline__ void cluster_stage0_load(const uint32_t (&rb)[Q], uin
         if (item >= TOTAL) break;
         const int b = item % NN;
         dft_reg<R>(v[it]);
-#pragma unroll
-        for (int k = 1; k < R; ++k) {
-            const float2 w = tw_smem ? tws[k * NN + b] : __ldg(tws + k * NN + b);
-            v[it][k] = cmul(v[it][k], w);
-        }
+        if (tw_smem) apply_twiddles<R, NN, true>(v[it], tws, b);
+        else apply_twiddles<R, NN, false>(v[it], tws, b);
     }
 }
 template <int C, int SPC, int NT, int IPT>

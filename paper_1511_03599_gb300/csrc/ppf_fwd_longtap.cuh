@@ -1,0 +1,223 @@
+// ppf_fwd_longtap.cuh -- fused PFB forward kernel for many taps (T = 17..64).
+//
+// With many taps the T-1 halo rows a batch of output spectra shares with the
+// previous batch (the overlap of neighbouring blocks, Sec. 3.2) no longer fit
+// in registers, and for 32-bit input not in shared memory either (63 rows of
+// 4 KB at C = 512).  So each batch of B = 16 output spectra streams all
+// B + T - 1 raw rows it needs through a 3-slot TMA ring in chunks of RC rows:
+// the rows new to the batch come from HBM, the halo rows from L2, where the
+// previous batches of the same CTA just brought them (each raw sample is read
+// from HBM once; L2 -> SM traffic is (B + T - 1) / B times the input).
+//
+// FIR (Alg. 1), per thread = one channel pair, taps outermost: a window of B
+// rows lives in registers; tap t adds h[t] * x[j + t] to output j for all B
+// outputs, then the dead row t is replaced by row t + B (slot (j + t) mod B
+// holds row j + t).  Each row is loaded and converted once per batch, each
+// tap loaded once per batch (from L1/L2), and every FMA is a packed
+// (re, im) x (h, h) pair.  Chunks are consumed in order: every thread waits
+// for a chunk's TMA barrier itself, and each warp arrives on the chunk
+// slot's "empty" barrier when it is done, so thread 0 refills a slot without
+// a CTA-wide barrier.  The filtered batch then goes through the same
+// warp-local DFT stages (Eq. 2) as the carry kernel.
+#pragma once
+
+#include "ppf_fwd_carry.cuh"
+
+namespace ppf {
+
+template <int C, int IN>
+struct LongShape {
+    static constexpr int NT = C / 2;                                 // one channel pair per thread
+    static constexpr int B = 16;                                     // output spectra per batch
+    static constexpr int BIN = InTraits<IN>::bytes;
+    static constexpr int RC = BIN <= 4 ? 16 : 8;                     // rows per ring chunk
+    static constexpr int NS = 3;                                     // ring slots
+    static constexpr int NWARP = NT / 32;
+    static constexpr int SPW = B / (NWARP > 0 ? NWARP : 1);          // spectra per warp in the DFT
+    static constexpr int YBYTES = B * C * 8;
+    static constexpr int TWBYTES = tw_size(C) * 8;
+    static constexpr int CHUNKB = RC * C * BIN;
+    static constexpr int RING_OFF = YBYTES + TWBYTES;
+    static constexpr int BAR_OFF = RING_OFF + NS * CHUNKB;           // NS full + NS empty + 1 + flag
+    static constexpr int SMEM = BAR_OFF + 8 * (2 * NS + 2);
+    static constexpr bool OK = C >= 64 && C <= 512 && NT % 32 == 0 && SPW >= 1 && SPW * NWARP == B &&
+                               warp_fft_ok(C, SPW) && SMEM <= 226 * 1024 && B % RC == 0;
+};
+
+template <int C, int IN, int OUT>
+__global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kernel(FwdArgs args) {
+    using S = LongShape<C, IN>;
+    constexpr int NT = S::NT, B = S::B, BIN = S::BIN, RC = S::RC, NS = S::NS, NWARP = S::NWARP;
+    constexpr int NST = fft_stages(C);
+    constexpr int OB = OUT == OUT_CF32 ? 8 : 4;
+    static_assert(S::OK, "shape not supported by the long-tap kernel");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* ybuf = reinterpret_cast<float2*>(smem);
+    float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
+    unsigned char* ring = smem + S::RING_OFF;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);    // [NS] chunk landed
+    uint64_t* empty = full + NS;                                         // [NS] every warp is done with it
+    uint64_t* inj = full + 2 * NS;                                       // never completed (testing aid)
+    volatile int* sdead = reinterpret_cast<volatile int*>(full + 2 * NS + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int cp = tid;
+    const long long n_spectra = args.n_spectra;
+    const int T = args.T;                        // 17 .. 64
+    const long long n_raw = n_spectra + T - 1;
+    const long long nbt = (n_spectra + B - 1) / B;
+    const int nch = (B + T - 1 + RC - 1) / RC;   // chunks per batch
+    const float2* taps2 = reinterpret_cast<const float2*>(args.taps);   // [t][pair]
+
+    for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NWARP);
+        }
+        mbar_init(inj, 1);
+        fence_mbar_init();
+        *sdead = 0;
+    }
+    __syncthreads();
+
+    // Chunk uses are counted over the whole kernel (g), so slots and barrier
+    // phases run on across the stream segments of the CTA's share.
+    long long g_base = 0;           // first chunk use of the current segment
+    long long issued = 0;           // thread 0: chunk uses issued so far (over the kernel)
+    long long seg_end = 0;          // chunk uses up to the end of the current segment
+    const unsigned char* seg_in = nullptr;
+    long long seg_lo = 0;
+    auto chunk_rows = [&](long long rel) -> long long {   // rows of chunk `rel` of the segment
+        const long long k = rel / nch, c = rel % nch;
+        const long long r0 = (seg_lo + k) * B + c * RC;
+        long long rows = n_raw - r0;
+        rows = rows < RC ? rows : RC;
+        const long long need = B + T - 1 - c * RC;        // rows of the batch in this chunk
+        rows = rows < need ? rows : need;
+        return rows < 0 ? 0 : rows;
+    };
+    auto issue = [&](long long g) {             // thread 0: chunk use g (of the current segment)
+        const long long rel = g - g_base;
+        const int s = (int)(g % NS);
+        const long long rows = chunk_rows(rel);
+        mbar_expect_tx(&full[s], (uint32_t)(rows * C * BIN));
+        if (rows > 0) {
+            const long long k = rel / nch, c = rel % nch;
+            const long long r0 = (seg_lo + k) * B + c * RC;
+            tma_load_1d(ring + s * S::CHUNKB, seg_in + (size_t)r0 * C * BIN, (uint32_t)(rows * C * BIN), &full[s]);
+        }
+    };
+    // thread 0: refill every slot whose previous use all warps have released
+    auto refill = [&](long long upto) {
+        for (; issued < upto && issued < seg_end; ++issued) {
+            if (issued >= NS) {
+                const long long prev = issued - NS;
+                if (!mbar_wait_bounded(&empty[prev % NS], (uint32_t)((prev / NS) & 1), kWaitLimitNs)) {
+                    atomicExch(args.err, 1);
+                    *sdead = 1;
+                    return;
+                }
+            }
+            fence_proxy_async_smem();
+            issue(issued);
+        }
+    };
+    auto wait_full = [&](long long g) {         // every thread: chunk use g has landed
+        if (*sdead) return;
+        if (!mbar_wait_bounded(&full[g % NS], (uint32_t)((g / NS) & 1), kWaitLimitNs)) {
+            atomicExch(args.err, 1);
+            *sdead = 1;
+        }
+    };
+    auto release = [&](long long g) {           // every thread: done with chunk use g
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cta(&empty[g % NS]);
+    };
+
+    BatchShare share(nbt, args.n_streams, blockIdx.x, gridDim.x);
+    long long strm, lo, hi;
+    bool first = true;
+    while (share.next(strm, lo, hi)) {
+        seg_in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
+        void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * OB;
+        seg_lo = lo;
+        seg_end = g_base + (hi - lo) * nch;
+        if (tid == 0) {
+            if (first && (args.flags & FWD_INJECT_TIMEOUT) && !mbar_wait_bounded(inj, 0, kInjectedWaitNs)) {
+                atomicExch(args.err, 1);
+                *sdead = 1;
+            }
+            if (!*sdead) refill(g_base + NS);
+        }
+        first = false;
+        __syncthreads();
+
+        for (long long k = lo; k < hi; ++k) {
+            const long long g0 = g_base + (k - lo) * nch;      // first chunk use of this batch
+            // ------------------------------------------------------------- FIR
+            unsigned long long acc[B][2];
+#pragma unroll
+            for (int j = 0; j < B; ++j) acc[j][0] = acc[j][1] = 0ull;
+            float4 xw[B];
+            // rows 0 .. B-1 of the batch fill the window (B / RC whole chunks)
+#pragma unroll
+            for (int c = 0; c < B / RC; ++c) {
+                wait_full(g0 + c);
+                const unsigned char* slot = ring + (int)((g0 + c) % NS) * S::CHUNKB + 2 * cp * BIN;
+#pragma unroll
+                for (int i = 0; i < RC; ++i) xw[c * RC + i] = load_pair_smem<IN>(slot + (size_t)i * C * BIN);
+                release(g0 + c);
+                if (tid == 0 && !*sdead) refill(g0 + c + 1 + NS);
+            }
+            // taps in blocks of B: tap t = tb + u uses window slot (j + u) mod B for output j,
+            // then slot u takes row t + B (chunk (t + B) / RC)
+            for (int tb = 0; tb < T; tb += B) {
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const int t = tb + u;
+                    if (t < T) {
+                        const float2 h = __ldg(taps2 + t * (C / 2) + cp);
+                        const unsigned long long h0 = pk2(h.x, h.x), h1 = pk2(h.y, h.y);
+#pragma unroll
+                        for (int j = 0; j < B; ++j) {
+                            const float4 x = xw[(j + u) % B];
+                            ffma2(acc[j][0], h0, pk2(x.x, x.y));
+                            ffma2(acc[j][1], h1, pk2(x.z, x.w));
+                        }
+                        const int r = t + B;                    // the row that takes slot u
+                        if (r < B + T - 1) {
+                            const long long g = g0 + r / RC;
+                            if (u % RC == 0) wait_full(g);      // r % RC == u % RC (B and tb are multiples of RC)
+                            xw[u] = load_pair_smem<IN>(ring + (int)(g % NS) * S::CHUNKB + 2 * cp * BIN +
+                                                       (size_t)(u % RC) * C * BIN);
+                            if (u % RC == RC - 1 || r == B + T - 2) {
+                                release(g);
+                                if (tid == 0 && !*sdead) refill(g + 1 + NS);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const float2 a = upk2(acc[j][0]), b2 = upk2(acc[j][1]);
+                *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b2.x, b2.y);
+            }
+            __syncthreads();
+            // ------------------------------------------------------------- FFT
+            const long long vhi = *sdead ? 0 : n_spectra;           // a CTA that gave up stores nothing
+            static_for<NST>([&](auto p) {
+                fft_stage<C, B, NT, decltype(p)::value, OUT, true, S::SPW>(ybuf, tw_s, out, k * B, 0, vhi);
+            });
+            __syncthreads();   // every warp is done with ybuf before the next FIR writes it
+        }
+        g_base = seg_end;
+    }
+    // leave only after every copy this CTA issued has landed
+    if (tid == 0)
+        for (long long g = (issued > NS ? issued - NS : 0); g < issued; ++g)
+            mbar_wait_bounded(&full[g % NS], (uint32_t)((g / NS) & 1), kWaitLimitNs);
+}
+
+}  // namespace ppf

@@ -41,8 +41,9 @@ struct BwdEntry {
 };
 // Adjoint kernels (complex FP32 input only); false when (C, tap bucket) is not built.
 bool bwd_lookup(int C, int tap_bucket, BwdEntry* e);
-// grad_h[t*C + c] = sum_p partials[p*TM*C + t*C + c], p in order.
-cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, float* grad_h, cudaStream_t st);
+// grad_h[t*C + c] = sum_p partials[p*TM*C + t*C + c], p in order (NaN when *err != 0).
+cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, const int* err, float* grad_h,
+                       cudaStream_t st);
 
 // Per-C lookups; return false when the (tap bucket, in, out) triple is not built.
 #define PPF_DECLARE_C(C)                                                         \

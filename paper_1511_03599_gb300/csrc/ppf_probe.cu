@@ -79,9 +79,11 @@ __global__ void k_cvt_s8(float* out, int iters, uint32_t seed) {
     if (s == 12345.678f) out[blockIdx.x] = s;
 }
 
-// int8 -> FP32 by the exponent-bias method: the biased byte (b ^ 0x80) is
-// placed in the low mantissa bits of 2^23 (0x4B000000) with a byte permute,
-// and 2^23 + 128 is subtracted; exact for all 256 byte values.
+// int8 -> FP32 by the exponent-bias ("magic number") method, a standard
+// integer-to-float technique (H. S. Warren, Hacker's Delight, 2nd ed., ch. 17,
+// converting between integer and floating point): the biased byte (b ^ 0x80)
+// is placed in the low mantissa bits of 2^23 (0x4B000000) with a byte
+// permute, and 2^23 + 128 is subtracted; exact for all 256 byte values.
 __device__ __forceinline__ float i8_bias(uint32_t wx, uint32_t sel) {
     return __int_as_float(__byte_perm(wx, 0x4B000000u, sel)) - 8388736.0f;
 }

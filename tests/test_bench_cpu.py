@@ -34,3 +34,28 @@ def test_oracle_sample_child():
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["seconds"] > 0
+
+
+def test_gpus_n_launches_n_ranks():
+    """--gpus 2 outside torchrun starts two ranks of bench.py itself (torch.distributed.run,
+    rendezvous on 127.0.0.1); the reference arm runs on rank 0 only and reports the world size."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.strip().splitlines() if x.startswith("{")]
+    assert len(lines) == 1, r.stdout           # rank 1 prints nothing
+    assert lines[0]["n_gpus"] == 2 and lines[0]["impl"] == "reference"
+
+
+def test_relaunch_command_and_world_check():
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = bench.relaunch_command(4, ["--steps", "3"], 29555)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert "--nproc-per-node=4" in cmd and cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[-2:] == ["--steps", "3"] and cmd[-3].endswith("bench.py")
+    # a measured run whose rank count differs from --gpus stops before touching a GPU
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0 and "--gpus 2 but 1 rank" in r.stderr

@@ -276,6 +276,20 @@ def test_rel_l2():
     assert oracle.rel_l2(np.array([3 + 4j, 1]), a) == pytest.approx(0.2)
 
 
+def test_rel_l2_max_per_spectrum():
+    # two spectra of two bins: errors 0.2 and 0.5 of their own norms
+    ref = np.array([[3 + 4j, 0], [0, 2]])
+    got = np.array([[3 + 4j, 1], [0, 2 + 1j]])
+    assert oracle.rel_l2_max_per_spectrum(ref, ref) == 0.0
+    assert oracle.rel_l2_max_per_spectrum(got, ref) == pytest.approx(0.5)
+    # the whole-output ratio is smaller: sqrt(1 + 1) / sqrt(25 + 4)
+    assert oracle.rel_l2(got, ref) == pytest.approx(np.sqrt(2 / 29))
+    # an all-zero reference spectrum contributes its absolute error
+    assert oracle.rel_l2_max_per_spectrum(np.array([[0, 3j]]), np.array([[0, 0]])) == pytest.approx(3.0)
+    with pytest.raises(ValueError):
+        oracle.rel_l2_max_per_spectrum(np.zeros((2, 3)), np.zeros((3, 2)))
+
+
 # ------------------------------------------------------- mutation tests ---
 # Each mutant is a plausible mistake planted in the oracle itself (via
 # monkeypatch); at least one pin above must fail for it.

@@ -5,9 +5,10 @@ loop with a device-memory budget fixed at start-up, or code where a cudaMalloc
 could synchronise the device or fail).  ppf_backward_noalloc keeps its
 tap-gradient partial sums in a fixed array inside the library instead of
 allocating them.  These tests call it through the C ABI, twice in a row with
-different shapes, and compare each result with ppf_backward, within the
-adjoint tests' tolerances (relative L2 1e-5 for the input gradient, 1e-4
-for the tap gradient).  The file is named to be collected last.
+different shapes, and compare each result with the FP64 oracle's gradients
+and with ppf_backward, within the adjoint tests' tolerances (relative L2 1e-5
+for the input gradient, 1e-4 for the tap gradient).  The file is named to be
+collected last.
 """
 import ctypes
 
@@ -41,6 +42,14 @@ def _call(ppf, fn, plan, G, x, S, ns):
     return gx, gh
 
 
+def _oracle_grads(G, x, h, C, T):
+    Gn = G.cpu().numpy().astype(np.complex128)
+    xn = x.cpu().numpy().astype(np.complex128)
+    gx = np.stack([oracle.pfb_grad_input(Gn[i], h, C, T) for i in range(Gn.shape[0])])
+    gh = sum(oracle.pfb_grad_taps(Gn[i], xn[i], C, T) for i in range(Gn.shape[0]))
+    return gx, gh
+
+
 def test_noalloc_backward_matches_backward_twice(ppf):
     rng = np.random.default_rng(2024)
     C, T = 256, 16
@@ -54,6 +63,9 @@ def test_noalloc_backward_matches_backward_twice(ppf):
             gx_n, gh_n = _call(ppf, "ppf_backward_noalloc", plan, G, x, S, ns)
             gx_r, gh_r = _call(ppf, "ppf_backward", plan, G, x, S, ns)
             plan.check_device()
+            ref_gx, ref_gh = _oracle_grads(G, x, h, C, T)
+            assert oracle.rel_l2(gx_n.cpu().numpy().reshape(ref_gx.shape), ref_gx) <= 1e-5
+            assert oracle.rel_l2(gh_n.cpu().numpy(), ref_gh) <= 1e-4
             assert oracle.rel_l2(gx_n.cpu().numpy(), gx_r.cpu().numpy()) <= 1e-5
             assert oracle.rel_l2(gh_n.cpu().numpy(), gh_r.cpu().numpy()) <= 1e-4
 
@@ -62,7 +74,8 @@ def test_noalloc_many_streams_match_backward(ppf):
     """CTAs share the batches of all streams, so any stream count fits the fixed array."""
     rng = np.random.default_rng(2025)
     C, T = 256, 16
-    with ppf.Plan(C, T, synth.design_taps(C, T), "cf32", "c64") as plan:
+    h = synth.design_taps(C, T)
+    with ppf.Plan(C, T, h, "cf32", "c64") as plan:
         ns, S = 300, 3          # more streams than resident CTAs
         x = torch.from_numpy((rng.standard_normal((ns, C * (S + T - 1)))
                               + 1j * rng.standard_normal((ns, C * (S + T - 1)))).astype(np.complex64)).cuda()
@@ -71,5 +84,8 @@ def test_noalloc_many_streams_match_backward(ppf):
         gx_n, gh_n = _call(ppf, "ppf_backward_noalloc", plan, G, x, S, ns)
         gx_r, gh_r = _call(ppf, "ppf_backward", plan, G, x, S, ns)
         plan.check_device()
+        ref_gx, ref_gh = _oracle_grads(G, x, h, C, T)
+        assert oracle.rel_l2(gx_n.cpu().numpy().reshape(ref_gx.shape), ref_gx) <= 1e-5
+        assert oracle.rel_l2(gh_n.cpu().numpy(), ref_gh) <= 1e-4
         assert oracle.rel_l2(gx_n.cpu().numpy(), gx_r.cpu().numpy()) <= 1e-5
         assert oracle.rel_l2(gh_n.cpu().numpy(), gh_r.cpu().numpy()) <= 1e-4
