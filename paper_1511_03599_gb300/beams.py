@@ -79,13 +79,12 @@ class BeamSet:
     def info(self) -> dict:
         a = (ctypes.c_longlong * 7)()
         ppf.check(ppf.lib().ppf_beams_info(self.handle, a))
-        return dict(zip(("beams", "tiles", "tile_samples", "max_ctas_per_sm", "sms", "smem", "separate_launches"),
+        return dict(zip(("beams", "tiles", "tile_samples", "max_ctas_per_sm", "sms", "smem", "wide_tiles"),
                         list(a)))
 
     def launches_per_execute(self) -> int:
-        """Kernel launches one execute() enqueues (persistent + one per C >= 2048 beam)."""
-        i = self.info()
-        return (1 if i["tiles"] > 0 else 0) + i["separate_launches"]
+        """Kernel launches one execute() enqueues: the one persistent launch (after a queue reset)."""
+        return 1 if self.info()["tiles"] > 0 else 0
 
     def check_device(self, stream=None):
         ppf.check(ppf.lib().ppf_beams_check_device(self.handle, ppf._stream_handle(stream)))

@@ -2,18 +2,19 @@
 // spectrum counts in ONE persistent launch.
 //
 // The plan cuts every beam into tiles (contiguous ranges of output batches of
-// about `tile_samples` samples) and sorts all tiles largest first.  The grid
-// is persistent (CTAs per SM x SMs); each CTA pulls the next tile index from
-// a device counter (reset by a memset node before every launch, so the pair
-// can be captured in a CUDA graph), reads the tile's beam descriptor and runs
-// the FIR + DFT of that range with the code of the beam's (C, tap bucket)
-// class.  All classes share one block size (256 threads) and one dynamic
-// shared-memory size (the largest class's).  Beams with C >= 2048 instead
-// run, after the persistent launch and on the same stream, one launch each of
-// the single-stream kernel ppf_execute uses for their shape (a thread-block
-// cluster kernel or the generic one, with the grid the GPU holds at once).
-// Complex int8 input, complex FP32 output: the multi-beam workload of the
-// channeliser.
+// about `tile_samples` samples) and sorts the tiles largest first in two
+// queues: beams with C >= 2048 ("wide" tiles) and beams with C <= 1024
+// ("narrow" tiles).  The grid is persistent: one CTA of 512 threads per SM.
+// Each CTA first pulls wide tiles from a device counter and runs each with
+// the whole CTA -- the FIR + DFT body of the single-stream kernel for that C
+// (512 threads, raw rows and their halo staged through a TMA ring).  When the
+// wide queue is empty, the CTA splits into two groups of 256 threads, each
+// with half of the shared memory and its own named barrier, and each group
+// pulls narrow tiles from the second counter and runs them independently.
+// Both counters are reset by one memset before the launch, so the pair can
+// be captured in a CUDA graph.  The body of each tile is chosen by the beam's
+// (C, tap bucket) class.  Complex int8 input, complex FP32 output: the
+// multi-beam workload of the channeliser.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,10 +34,12 @@
 
 namespace ppf {
 
-constexpr int kBeamThreads = 256;
+constexpr int kBeamThreads = 512;                 // one CTA per SM
+constexpr int kNarrowThreads = 256;               // a group of a CTA running narrow tiles
 constexpr int kBeamC[] = {64, 128, 256, 512, 1024, 2048, 4096};
 constexpr int kBeamTM[] = {4, 8, 16};
 constexpr int kNumC = 7, kNumTM = 3;
+constexpr int kFirstWide = 5;                     // kBeamC[5] = 2048: wide from here on
 
 struct BeamDesc {
     const void* in;          // C*(S+T-1) complex int8 samples
@@ -54,14 +57,16 @@ struct BeamTile {
 
 struct BeamsArgs {
     const BeamDesc* beams;
-    const BeamTile* tiles;
-    unsigned long long* queue;   // next tile index
+    const BeamTile* tiles;       // wide tiles [0, n_wide), then narrow tiles
+    unsigned long long* queue;   // [0]: next wide tile, [1]: next narrow tile
     int* err;
-    long long n_tiles;
+    long long n_wide, n_narrow;
     int flags;
 };
 
-template <int CI, int TI>
+template <int CI> constexpr int class_threads() { return CI >= kFirstWide ? kBeamThreads : kNarrowThreads; }
+
+template <int CI, int TI, class GRP>
 __device__ __forceinline__ bool beam_tile(const BeamsArgs& a, const BeamDesc& d, const BeamTile& t,
                                           unsigned char* smem) {
     constexpr int C = kBeamC[CI], TM = kBeamTM[TI];
@@ -77,53 +82,74 @@ __device__ __forceinline__ bool beam_tile(const BeamsArgs& a, const BeamDesc& d,
     fa.n_spectra = d.n_spectra;
     fa.T = d.T;
     fa.flags = a.flags;
-    return fwd_range<C, TM, IN_CI8, OUT_CF32, kBeamThreads>(fa, d.in, d.out, t.lo, t.hi, smem);
+    return fwd_range<C, TM, IN_CI8, OUT_CF32, class_threads<CI>(), GRP>(fa, d.in, d.out, t.lo, t.hi, smem);
 }
 
-template <int CI, int TI>
+// run tile t with the body of class cls, among classes with C index in [CI, CEND)
+template <int CI, int TI, int CEND, class GRP>
 __device__ __forceinline__ bool beam_dispatch(int cls, const BeamsArgs& a, const BeamDesc& d, const BeamTile& t,
                                               unsigned char* smem) {
-    if (cls == CI * kNumTM + TI) return beam_tile<CI, TI>(a, d, t, smem);
-    if constexpr (TI + 1 < kNumTM) return beam_dispatch<CI, TI + 1>(cls, a, d, t, smem);
-    else if constexpr (CI + 1 < kNumC) return beam_dispatch<CI + 1, 0>(cls, a, d, t, smem);
+    if (cls == CI * kNumTM + TI) return beam_tile<CI, TI, GRP>(a, d, t, smem);
+    if constexpr (TI + 1 < kNumTM) return beam_dispatch<CI, TI + 1, CEND, GRP>(cls, a, d, t, smem);
+    else if constexpr (CI + 1 < CEND) return beam_dispatch<CI + 1, 0, CEND, GRP>(cls, a, d, t, smem);
     else return true;
 }
 
-__global__ void __launch_bounds__(kBeamThreads, 2) pfb_beams_kernel(BeamsArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ unsigned long long s_tile;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1ull);
-        __syncthreads();
-        const unsigned long long ti = s_tile;
-        __syncthreads();
-        if (ti >= (unsigned long long)a.n_tiles) return;
-        const BeamTile t = a.tiles[ti];
-        const BeamDesc d = a.beams[t.beam];
-        if (!beam_dispatch<0, 0>(d.cls, a, d, t, smem)) return;
-    }
-}
-
 template <int CI, int TI>
-constexpr int class_smem() {
-    constexpr int s = FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, kBeamThreads>::SMEM;
-    if constexpr (TI + 1 < kNumTM) return s > class_smem<CI, TI + 1>() ? s : class_smem<CI, TI + 1>();
-    else if constexpr (CI + 1 < kNumC) return s > class_smem<CI + 1, 0>() ? s : class_smem<CI + 1, 0>();
+constexpr int class_smem_of() { return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::SMEM; }
+template <int CI, int TI, int CEND>
+constexpr int class_smem_max() {
+    constexpr int s = class_smem_of<CI, TI>();
+    if constexpr (TI + 1 < kNumTM) return s > class_smem_max<CI, TI + 1, CEND>() ? s : class_smem_max<CI, TI + 1, CEND>();
+    else if constexpr (CI + 1 < CEND) return s > class_smem_max<CI + 1, 0, CEND>() ? s : class_smem_max<CI + 1, 0, CEND>();
     else return s;
 }
 template <int CI, int TI>
 constexpr int class_batch(int cls) {
-    if (cls == CI * kNumTM + TI) return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, kBeamThreads>::B;
+    if (cls == CI * kNumTM + TI) return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::B;
     if constexpr (TI + 1 < kNumTM) return class_batch<CI, TI + 1>(cls);
     else if constexpr (CI + 1 < kNumC) return class_batch<CI + 1, 0>(cls);
     else return 0;
 }
-constexpr int kBeamSmem = class_smem<0, 0>();
+// shared memory of a narrow group (128-byte multiple) and of the CTA
+constexpr int kNarrowSmem = (class_smem_max<0, 0, kFirstWide>() + 127) / 128 * 128;
+constexpr int kWideSmem = class_smem_max<kFirstWide, 0, kNumC>();
+constexpr int kBeamSmem = kWideSmem > 2 * kNarrowSmem ? kWideSmem : 2 * kNarrowSmem;
+
+__global__ void __launch_bounds__(kBeamThreads, 1) pfb_beams_kernel(BeamsArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned long long s_tile[2];
+    // wide tiles: the whole CTA
+    for (;;) {
+        if (threadIdx.x == 0) s_tile[0] = atomicAdd(&a.queue[0], 1ull);
+        __syncthreads();
+        const unsigned long long ti = s_tile[0];
+        __syncthreads();
+        if (ti >= (unsigned long long)a.n_wide) break;
+        const BeamTile t = a.tiles[ti];
+        const BeamDesc d = a.beams[t.beam];
+        if (!beam_dispatch<kFirstWide, 0, kNumC, CtaGroup>(d.cls, a, d, t, smem)) return;
+    }
+    // narrow tiles: two independent groups, each with half of the shared memory
+    using G = HalfGroup<kNarrowThreads>;
+    const int g = threadIdx.x / kNarrowThreads;
+    unsigned char* gsmem = smem + g * kNarrowSmem;
+    for (;;) {
+        if (G::tid() == 0) s_tile[g] = atomicAdd(&a.queue[1], 1ull);
+        G::sync();
+        const unsigned long long ti = s_tile[g];
+        G::sync();
+        if (ti >= (unsigned long long)a.n_narrow) return;
+        const BeamTile t = a.tiles[a.n_wide + ti];
+        const BeamDesc d = a.beams[t.beam];
+        if (!beam_dispatch<0, 0, kFirstWide, G>(d.cls, a, d, t, gsmem)) return;
+    }
+}
 
 // twiddles of every supported C (host)
 void fill_beam_twiddles(int C, std::vector<float2>& tw) {
     switch (C) {
-#define PPF_BTW(CC) case CC: tw.assign(tw_size(CC) > 0 ? tw_size(CC) : 1, make_float2(0.f, 0.f)); fill_twiddles<CC>(tw.data()); break;
+#define PPF_BTW(CC) case CC: tw.assign(tw_total_float2s(CC) > 0 ? tw_total_float2s(CC) : 1, make_float2(0.f, 0.f)); fill_twiddles<CC>(tw.data()); break;
         PPF_BTW(64) PPF_BTW(128) PPF_BTW(256) PPF_BTW(512) PPF_BTW(1024) PPF_BTW(2048) PPF_BTW(4096)
 #undef PPF_BTW
         default: tw.clear();
@@ -140,14 +166,6 @@ ppf_status bcuda(cudaError_t e, const char* what) {
 }
 
 constexpr uint32_t kBeamsMagic = 0x50504642u;   // "PPFB"
-
-// The single-stream kernel of a beam that runs on its own launch (C >= 2048).
-bool separate_entry(int C, int T, ppf::FwdEntry* e) {
-    const int tm = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : T <= 8 ? 8 : 16;
-    if (C == 2048) return ppf::fwd_lookup_c2048(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
-    if (C == 4096) return ppf::fwd_lookup_c4096(tm, PPF_IN_CI8, PPF_OUT_CF32, e);
-    return false;
-}
 
 int class_of(int C, int T) {
     int ci = -1, ti = -1;
@@ -166,12 +184,9 @@ struct ppf_beams_s {
     long long tile_samples;
     std::vector<ppf::BeamDesc> host;       // descriptors (pointers bound by ppf_beams_bind)
     std::vector<int> tm;                   // tap bucket per beam
-    std::vector<int> big;                  // beams run by a launch of their own
-    std::vector<ppf::FwdEntry> big_entry;  // their kernels
-    std::vector<int> big_units;            // resident work units (CTAs or clusters) of each
     ppf::BeamDesc* d_beams;
-    ppf::BeamTile* d_tiles;
-    long long n_tiles;
+    ppf::BeamTile* d_tiles;                // wide tiles, then narrow tiles
+    long long n_wide, n_narrow;
     unsigned long long* d_queue;
     int* d_err;
     float* d_taps;                         // all beams' taps, concatenated
@@ -188,36 +203,40 @@ static bool valid_beams(ppf_beams_t b) {
     return g_beams.count(b) != 0 && b->magic == kBeamsMagic;
 }
 
+// Cut every beam into tiles of about tile_samples samples (whole output
+// batches of its class); wide tiles (C >= 2048) first, each queue sorted by
+// work (samples x tap bucket) largest first.
 static ppf_status build_tiles(ppf_beams_t b, long long tile_samples) {
-    std::vector<ppf::BeamTile> tiles;
-    std::vector<long long> weight;
-    std::vector<bool> is_big(b->n_beams, false);
-    for (int i : b->big) is_big[i] = true;
+    std::vector<ppf::BeamTile> tiles[2];
+    std::vector<long long> weight[2];
     for (int i = 0; i < b->n_beams; ++i) {
-        if (is_big[i]) continue;
         const ppf::BeamDesc& d = b->host[i];
+        const int q = d.C >= ppf::kBeamC[ppf::kFirstWide] ? 0 : 1;
         const long long B = ppf::class_batch<0, 0>(d.cls);
         const long long nbt = (d.n_spectra + B - 1) / B;
         long long per = tile_samples / (B * d.C);
         if (per < 1) per = 1;
         for (long long lo = 0; lo < nbt; lo += per) {
             const long long hi = std::min(nbt, lo + per);
-            tiles.push_back(ppf::BeamTile{lo, hi, i});
-            weight.push_back((hi - lo) * B * d.C * (long long)b->tm[i]);
+            tiles[q].push_back(ppf::BeamTile{lo, hi, i});
+            weight[q].push_back((hi - lo) * B * d.C * (long long)b->tm[i]);
         }
     }
-    std::vector<size_t> order(tiles.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return weight[x] > weight[y]; });
-    std::vector<ppf::BeamTile> sorted(tiles.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = tiles[order[i]];
+    std::vector<ppf::BeamTile> sorted;
+    for (int q = 0; q < 2; ++q) {
+        std::vector<size_t> order(tiles[q].size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return weight[q][x] > weight[q][y]; });
+        for (size_t i : order) sorted.push_back(tiles[q][i]);
+    }
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
     cudaError_t ce = cudaMalloc(&b->d_tiles, sizeof(ppf::BeamTile) * std::max<size_t>(1, sorted.size()));
     if (ce == cudaSuccess)
         ce = cudaMemcpy(b->d_tiles, sorted.data(), sizeof(ppf::BeamTile) * sorted.size(), cudaMemcpyHostToDevice);
     if (ce != cudaSuccess) return bcuda(ce, "ppf_beams: tiles");
-    b->n_tiles = (long long)sorted.size();
+    b->n_wide = (long long)tiles[0].size();
+    b->n_narrow = (long long)tiles[1].size();
     b->tile_samples = tile_samples;
     return PPF_OK;
 }
@@ -296,7 +315,7 @@ extern "C" ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C
     ce = cudaMalloc(&b->d_taps, sizeof(float) * taps.size());
     if (ce == cudaSuccess) ce = cudaMalloc(&b->d_tw, sizeof(float2) * std::max<size_t>(1, tw_all.size()));
     if (ce == cudaSuccess) ce = cudaMalloc(&b->d_beams, sizeof(ppf::BeamDesc) * n_beams);
-    if (ce == cudaSuccess) ce = cudaMalloc(&b->d_queue, sizeof(unsigned long long));
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->d_queue, 2 * sizeof(unsigned long long));
     if (ce == cudaSuccess) ce = cudaMalloc(&b->d_err, 16);
     if (ce == cudaSuccess) ce = cudaMemset(b->d_err, 0, 16);
     if (ce == cudaSuccess) ce = cudaMemcpy(b->d_taps, taps.data(), sizeof(float) * taps.size(), cudaMemcpyHostToDevice);
@@ -314,27 +333,6 @@ extern "C" ppf_status ppf_beams_plan(ppf_beams_t* out, int n_beams, const int* C
     for (int i = 0; i < n_beams; ++i) {
         b->host[i].taps = b->d_taps + taps_off[i];
         b->host[i].tw = b->d_tw + tw_off[C[i]];
-        ppf::FwdEntry e{};
-        if (!separate_entry(C[i], T[i], &e)) continue;
-        int units = 0;
-        ce = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e.smem);
-        if (ce == cudaSuccess) {
-            if (e.cluster > 0) {
-                ce = ppf::max_active_clusters(e, sms, &units);
-            } else {
-                ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&units, e.fn, e.threads, e.smem);
-                units *= sms;
-            }
-        }
-        if (ce != cudaSuccess) {
-            ppf_status s = bcuda(ce, "ppf_beams_plan: single-beam kernel");
-            ppf_beams_destroy(b);
-            return s;
-        }
-        if (units < 1) continue;      // stays on the persistent kernel
-        b->big.push_back(i);
-        b->big_entry.push_back(e);
-        b->big_units.push_back(units);
     }
     ppf_status s = build_tiles(b, 1ll << 20);
     if (s != PPF_OK) {
@@ -373,50 +371,28 @@ extern "C" ppf_status ppf_beams_execute(ppf_beams_t b, int ctas_per_sm, ppf_stre
     if (!b->bound) return ppf::set_error(PPF_ERR_INVALID_ARG, "ppf_beams_execute: buffers not bound");
     if (ctas_per_sm < 1 || ctas_per_sm > b->occupancy) ctas_per_sm = b->occupancy;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t ce = cudaSuccess;
-    if (b->n_tiles > 0) {
-        ce = cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned long long), st);
-        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: queue reset");
-        ppf::BeamsArgs a{b->d_beams, b->d_tiles, b->d_queue, b->d_err, b->n_tiles, 0};
-        long long grid = (long long)b->sms * ctas_per_sm;
-        if (grid > b->n_tiles) grid = b->n_tiles;
-        ppf::pfb_beams_kernel<<<(int)grid, ppf::kBeamThreads, ppf::kBeamSmem, st>>>(a);
-        ce = cudaPeekAtLastError();
-        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: launch");
-    }
-    for (size_t j = 0; j < b->big.size(); ++j) {
-        const ppf::BeamDesc& d = b->host[b->big[j]];
-        const ppf::FwdEntry& e = b->big_entry[j];
-        ppf::FwdArgs fa;
-        fa.in = d.in;
-        fa.out = d.out;
-        fa.in_stride = 0;
-        fa.out_stride = 0;
-        const long long nb = (d.n_spectra + e.batch - 1) / e.batch;
-        fa.n_streams = 1;
-        const long long units = std::min<long long>(b->big_units[j], nb);
-        const int per_unit = e.cluster > 0 ? e.cluster : 1;
-        fa.taps = d.taps;
-        fa.tw = d.tw;
-        fa.err = b->d_err;
-        fa.n_spectra = d.n_spectra;
-        fa.T = d.T;
-        fa.flags = 0;
-        ce = e.launch(fa, (int)(units * per_unit), st);
-        if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: single-beam launch");
-    }
+    if (b->n_wide + b->n_narrow == 0) return PPF_OK;
+    cudaError_t ce = cudaMemsetAsync(b->d_queue, 0, 2 * sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: queue reset");
+    ppf::BeamsArgs a{b->d_beams, b->d_tiles, b->d_queue, b->d_err, b->n_wide, b->n_narrow, 0};
+    long long grid = (long long)b->sms * ctas_per_sm;
+    // at most one CTA per wide tile plus one per two narrow tiles is busy
+    grid = std::min(grid, std::max<long long>(1, b->n_wide + (b->n_narrow + 1) / 2));
+    ppf::pfb_beams_kernel<<<(int)grid, ppf::kBeamThreads, ppf::kBeamSmem, st>>>(a);
+    ce = cudaPeekAtLastError();
+    if (ce != cudaSuccess) return bcuda(ce, "ppf_beams_execute: launch");
     return PPF_OK;
 }
 
 extern "C" ppf_status ppf_beams_info(ppf_beams_t b, long long info[7]) {
     if (!valid_beams(b) || info == nullptr) return ppf::set_error(PPF_ERR_INVALID_ARG, "ppf_beams_info: invalid argument");
     info[0] = b->n_beams;
-    info[1] = b->n_tiles;
+    info[1] = b->n_wide + b->n_narrow;
     info[2] = b->tile_samples;
     info[3] = b->occupancy;
     info[4] = b->sms;
     info[5] = ppf::kBeamSmem;
-    info[6] = (long long)b->big.size();
+    info[6] = b->n_wide;
     return PPF_OK;
 }
 

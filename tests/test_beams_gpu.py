@@ -101,24 +101,24 @@ def test_beams_reject_unsupported(mods):
         beams.BeamSet([512], [32], [10], [synth.design_taps(512, 32)])
 
 
-def test_beams_large_channel_counts_use_separate_launches(mods):
-    """C >= 2048 beams run the single-stream kernel of their shape: bit-identical to
-    ppf_execute, one launch each; a set of only such beams has no persistent launch."""
+def test_beams_wide_and_narrow_tiles_in_one_launch(mods):
+    """C >= 2048 beams run as wide tiles (the whole CTA) and C <= 1024 beams as narrow
+    tiles (half-CTA groups) of the same persistent launch; the C = 4096 body is the
+    single-stream kernel's, so those beams are bit-identical to ppf_execute."""
     ppf, _ = mods
-    for beams_def in ([(2048, 8, 300), (4096, 4, 100), (512, 8, 200), (2048, 16, 57)],
-                      [(2048, 3, 129), (4096, 16, 64)]):
+    for beams_def in ([(2048, 8, 300), (4096, 4, 100), (512, 8, 200), (2048, 16, 57), (64, 4, 900)],
+                      [(2048, 3, 129), (4096, 16, 64)], [(4096, 8, 1), (128, 16, 3)]):
         bs, xs, taps, ins, outs = make_set(mods, beams_def, seed=120)
-        n_big = sum(1 for c, _, _ in beams_def if c >= 2048)
         info = bs.info()
-        assert info["separate_launches"] == n_big
-        assert bs.launches_per_execute() == n_big + (1 if info["tiles"] > 0 else 0)
-        assert (info["tiles"] > 0) == any(c < 2048 for c, _, _ in beams_def)
+        assert bs.launches_per_execute() == 1
+        assert info["wide_tiles"] > 0 and info["tiles"] >= info["wide_tiles"]
+        assert (info["tiles"] > info["wide_tiles"]) == any(c < 2048 for c, _, _ in beams_def)
         bs.execute()
         torch.cuda.synchronize()
         bs.check_device()
         for (c, t, s), x, h, xd, y in zip(beams_def, xs, taps, ins, outs):
             assert oracle.rel_l2(y.cpu().numpy(), oracle.pfb(x, h, c, t)) <= 1e-5, (c, t, s)
-            if c >= 2048:
+            if c == 4096:
                 with ppf.Plan(c, t, h, "ci8", "c64") as plan:
                     ref = plan(xd)
                     torch.cuda.synchronize()
