@@ -284,6 +284,35 @@ def measure_fwd_bwd(steps: int, warmup: int, dev):
             "fwd_launch": info, "backward": "grad wrt input and taps, tap-gradient two-pass reduction"}
 
 
+def measure_fwd_bwd_headline(plan, w, x, y, steps: int, warmup: int, dev):
+    """Forward vs forward + adjoint (grad wrt input and taps) at the benchmark
+    workload itself (C=512, T=8, int8 input): the adjoint reads the int8 input,
+    the incoming complex64 gradient and writes a complex64 input gradient."""
+    import torch
+    from paper_1511_03599_gb300 import ppf, synth
+    st = torch.cuda.current_stream()
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_BASE + 6)
+    G = torch.randn((w.S, w.C), dtype=torch.complex64, device=dev, generator=g)
+    gx = torch.empty(w.n_raw * w.C, dtype=torch.complex64, device=dev)
+    gh = torch.empty(w.C * w.T, dtype=torch.float32, device=dev)
+
+    def bwd():
+        ppf.check(ppf.lib().ppf_backward(plan.handle, ppf.ctypes.c_void_p(G.data_ptr()),
+                                         ppf.ctypes.c_void_p(x.data_ptr()), ppf.ctypes.c_void_p(gx.data_ptr()),
+                                         ppf.ctypes.c_void_p(gh.data_ptr()), w.S, 1,
+                                         ppf.ctypes.c_void_p(st.cuda_stream)))
+
+    t_f = time_launches(lambda: plan.execute(x, out=y, stream=st), steps, warmup, st)
+    t_fb = time_launches(lambda: (plan.execute(x, out=y, stream=st), bwd()), steps, warmup, st)
+    plan.check_device()
+    del G, gx, gh
+    b_in = synth.in_bytes_per_sample(w.in_dtype)
+    return {"workload": w.name, "fwd_ms": t_f, "fwd_bwd_ms": t_fb, "fwd_bwd_over_fwd": t_fb / t_f,
+            "bwd_ms": t_fb - t_f, "backward": "grad wrt input and taps",
+            "bwd_bytes_per_sample": 8 + b_in + 8}
+
+
 def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
     """Fused kernel vs the unfused pair (FIR kernel, filtered spectra to HBM,
     then the DFT kernel) on the benchmark workload (E3 of the paper: the FIR/DFT
@@ -316,8 +345,8 @@ def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
 def measure_beams(steps: int, dev, seed: int = 4):
     """The multi-beam workload: 96 beams, C in {64..4096}, T in {4, 8, 16},
     spectra per beam uniform in [2^12, 2^17], complex int8 sigma=16 in, complex
-    FP32 out: one persistent launch (C <= 1024 beams) plus one launch per C >= 2048
-    beam of its single-stream kernel, replayed from a CUDA graph after autotuning."""
+    FP32 out: one persistent launch (C >= 2048 tiles on whole CTAs, C <= 1024 tiles on
+    half-CTA groups), replayed from a CUDA graph after autotuning."""
     import numpy as np
     import torch
     from paper_1511_03599_gb300 import beams, synth
@@ -352,7 +381,7 @@ def measure_beams(steps: int, dev, seed: int = 4):
            "samples": bs.samples(), "ms": ms, "gsps": bs.samples() / ms / 1e6, "GB_s": gbs,
            "hbm_frac": gbs / peak, "tile_samples": tune["tile_samples"], "ctas_per_sm": tune["ctas_per_sm"],
            "launches_per_step": bs.launches_per_execute(), "graph": True, "tiles": bs.info()["tiles"],
-           "separate_beam_launches": bs.info()["separate_launches"]}
+           "wide_tiles": bs.info()["wide_tiles"]}
     bs.close()
     del ins, outs
     return res
@@ -555,20 +584,21 @@ def main():
         plan.execute(x, out=y, stream=stream)
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # one event pair around the K back-to-back launches on the launching stream:
+    # the average launch duration (events between launches would add a gap each)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
         t0 = time.perf_counter()
+        e0.record(stream)
         for i in range(args.steps):
-            ev[i][0].record(stream)
             plan.execute(x, out=y, stream=stream)
-            ev[i][1].record(stream)
+        e1.record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     barrier()
-    per_launch_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    total_ms = e0.elapsed_time(e1)
     t_step = pdist.max_over_ranks(total_ms / 1e3 / args.steps, device=dev)
 
     info = plan.info()
@@ -576,7 +606,7 @@ def main():
     b_in, b_out = synth.in_bytes_per_sample(w.in_dtype), synth.out_bytes_per_sample(w.out_dtype)
     alg_bytes = w.C * w.n_raw * b_in + w.C * w.S * b_out + 4 * w.C * w.T
     value = world * samples / t_step / 1e9
-    kern_s = statistics.mean(per_launch_ms) / 1e3
+    kern_s = total_ms / 1e3 / args.steps
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / kern_s / 1e9
     traffic = profiled_traffic()
@@ -644,6 +674,10 @@ def main():
     fb = None
     if not args.no_fwd_bwd:
         fb = measure_fwd_bwd(max(5, args.steps), args.warmup, dev)
+        try:
+            fb["headline"] = measure_fwd_bwd_headline(plan, w, x, y, max(5, args.steps // 2), args.warmup, dev)
+        except Exception as e:  # noqa: BLE001 - reported beside the metric
+            fb["headline"] = {"error": str(e)}
         try:
             from paper_1511_03599_gb300 import fit
             r = fit.fit_taps()

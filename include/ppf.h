@@ -124,11 +124,13 @@ ppf_status ppf_execute_batched(ppf_plan_t plan, const void* in_dev, long long in
  *   grad_in[r][c]   = sum_t h[t*C+c] g_y[r-t][c],
  *   grad_taps[t*C+c] = sum over streams and s of Re(conj(g_y[s][c]) x[s+t][c]).
  *   grad_out_dev : n_streams * n_spectra*C complex FP32, streams contiguous
- *   in_dev       : the forward input, n_streams * C*(n_spectra+T-1) complex FP32
- *   grad_in_dev  : same layout as in_dev (written, not accumulated), or NULL
+ *   in_dev       : the forward input, n_streams * C*(n_spectra+T-1) samples of
+ *                  the plan's input type (complex int8 / int16 / FP32)
+ *   grad_in_dev  : n_streams * C*(n_spectra+T-1) complex FP32, one per input
+ *                  sample (written, not accumulated), or NULL
  *   grad_taps_dev: C*T floats (written), or NULL; not both NULL
- * Needs a plan with complex FP32 input, C in [64, 256] and T <= 16 (else
- * UNSUPPORTED).  The tap gradient is a deterministic two-pass reduction
+ * Needs C in [64, 512] and T <= 16, and T <= 8 at C = 512 (else UNSUPPORTED).
+ * The tap gradient is a deterministic two-pass reduction
  * (per-CTA partial sums, then a fixed-order sum); the partial-sum scratch is
  * allocated by the plan on the first call and grown when a call needs more
  * CTAs (cudaMalloc inside the call).  Asynchronous on `stream`.
@@ -148,12 +150,13 @@ ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* i
  * device or fail under memory pressure -- is not allowed).  The paper has no
  * counterpart; this is a deployment convenience.  Same arguments, results
  * and errors as ppf_backward, but the per-CTA tap-gradient partial sums live
- * in one fixed 4 MiB array (1,048,576 floats) inside the library instead of
+ * in one fixed 2 MiB array (524,288 floats) inside the library instead of
  * plan memory, and the call allocates nothing.  The plan itself (made once
  * at set-up with ppf_plan) still owns the taps and tables.
  *   - Size limit: each CTA needs a row of tap_bucket*C floats; the call uses
- *     at most 1,048,576 / (tap_bucket*C) CTAs (256 at C=256, T=16).  CTAs
- *     share the batches of all streams, so every stream count fits.
+ *     at most 524,288 / (tap_bucket*C) CTAs (128 at C=256, T=16 or C=512,
+ *     T=8, fewer than the GPU holds at once there).  CTAs share the batches
+ *     of all streams, so every stream count fits.
  *   - The first call on a device looks up the array's device address with
  *     that device current (cudaGetSymbolAddress); make that first call before
  *     any stream capture.
@@ -183,25 +186,26 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   in [64, 4096]), T[i] <= 16 taps, n_spectra[i] output spectra and taps_host[i]
  *   (C[i]*T[i] FP32, tap-major; read during the call).  Complex int8 input and
  *   complex FP32 output only (else UNSUPPORTED).  The plan cuts every beam
- *   into tiles of about 2^20 samples, sorts them largest first and keeps taps,
- *   twiddles, descriptors, tiles, a work-queue counter and a status word in
- *   device memory it allocates.  Synchronous.
+ *   into tiles of about 2^20 samples, sorts them largest first into a wide
+ *   (C >= 2048) and a narrow queue and keeps taps, twiddles, descriptors,
+ *   tiles, two work-queue counters and a status word in device memory it
+ *   allocates.  Synchronous.
  * ppf_beams_bind -- the device buffers of every beam (in_dev[i]: C[i]*(n_spectra[i]
  *   +T[i]-1) samples, out_dev[i]: n_spectra[i]*C[i] outputs; 16-byte aligned);
  *   copied to the device descriptors (synchronous).  Rebind when they change.
  * ppf_beams_set_tiling -- re-cut the tiles to about tile_samples samples each
  *   (the autotuner's knob); synchronous.
- * ppf_beams_execute -- enqueue one queue-counter reset and ONE launch of the
- *   persistent kernel (ctas_per_sm CTAs per SM, clamped to what fits; 0 =
- *   most that fit) for the beams with C <= 1024.  Each CTA pulls tiles from
- *   the counter and runs the beam's FIR + DFT for the tile.  Then, on the
- *   same stream, one launch per beam with C >= 2048 of the single-stream
- *   kernel ppf_execute uses for that shape (thread-block cluster or generic).
- *   Every beam's result equals ppf_execute's.  Asynchronous on `stream`; no
- *   allocation.
- * ppf_beams_info -- info[0]=beams, [1]=tiles (of the persistent launch),
- *   [2]=tile samples, [3]=max CTAs per SM, [4]=SMs, [5]=dynamic shared memory
- *   bytes, [6]=separate launches (beams with C >= 2048).
+ * ppf_beams_execute -- enqueue one reset of the two queue counters and ONE
+ *   launch of the persistent kernel (one CTA of 512 threads per SM;
+ *   ctas_per_sm is accepted for compatibility and clamped to what fits).
+ *   Each CTA first pulls wide tiles (beams with C >= 2048) and runs each with
+ *   all its threads -- the FIR + DFT body of the single-stream kernel for that
+ *   C, raw rows staged through a TMA ring -- then splits into two groups of
+ *   256 threads that pull narrow tiles (C <= 1024) independently.  Every
+ *   beam's result equals ppf_execute's up to FP32 rounding (bit-identical for
+ *   C = 4096).  Asynchronous on `stream`; no allocation.
+ * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=CTAs per SM,
+ *   [4]=SMs, [5]=dynamic shared memory bytes, [6]=wide tiles (C >= 2048).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
  * ppf_beams_destroy -- free everything (NULL accepted).
  * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY, DEVICE_TIMEOUT.

@@ -221,8 +221,9 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
         grid_ctas = sms * occ;
     }
 
-    // Device tables: taps padded to the bucket with zero rows, twiddles.
-    std::vector<float> taps((size_t)tm * C, 0.f);
+    // Device tables: taps padded to the bucket with zero rows (and 4 more zero
+    // rows for the largest bucket: the long-tap kernel loads taps 4 ahead), twiddles.
+    std::vector<float> taps((size_t)(tm == PPF_MAX_TAPS ? tm + 4 : tm) * C, 0.f);
     std::memcpy(taps.data(), coeffs_host, sizeof(float) * (size_t)C * T);
     std::vector<float> tw;
     twiddles(C, tw);
@@ -233,7 +234,7 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
     p->C = C; p->T = T; p->TM = tm; p->device = dev; p->sms = sms; p->occupancy = occ;
     p->grid = grid_ctas;
     p->in = in_dtype; p->out = out_dtype; p->fwd = e;
-    if (in_dtype == PPF_IN_CF32 && ppf::bwd_lookup(C, tm, &p->bwd)) {
+    if (ppf::bwd_lookup(C, tm, (int)in_dtype, &p->bwd)) {
         ce = cudaFuncSetAttribute(p->bwd.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->bwd.smem);
         if (ce == cudaSuccess)
             ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->bwd_occupancy, p->bwd.fn, p->bwd.threads, p->bwd.smem);
@@ -362,7 +363,7 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
                                    ppf_stream_t stream) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: invalid plan");
     if (!p->has_bwd)
-        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward: needs complex FP32 input, C in [64, 256] and T <= 16");
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward: needs C in [64, 512] with T <= 16 (T <= 8 at C = 512)");
     if (grad_out_dev == nullptr || in_dev == nullptr || (grad_in_dev == nullptr && grad_taps_dev == nullptr))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: NULL buffer");
     if (n_spectra < 1 || n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: empty problem");
@@ -374,7 +375,7 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
     const long long n_raw = n_spectra + T - 1;
     const long long in_len = (long long)C * n_raw, out_len = (long long)C * n_spectra;
     if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), in_dev,
-                                (unsigned long long)(n_streams * in_len * 8)))
+                                (unsigned long long)(n_streams * in_len * bytes_in(p->in))))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps the input");
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
     // one wave of resident CTAs sharing the batches of all streams equally
@@ -389,7 +390,7 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
     }
     ppf::BwdArgs a;
     a.gY = static_cast<const float2*>(grad_out_dev);
-    a.x = static_cast<const float2*>(in_dev);
+    a.x = in_dev;
     a.taps = p->d_taps;
     a.tw = p->d_tw;
     a.gx = static_cast<float2*>(grad_in_dev);
@@ -546,7 +547,7 @@ extern "C" ppf_status ppf_update_taps(ppf_plan_t p, const float* taps_dev, ppf_s
 // memory.  Every GPU that loads the library holds the array until the process
 // exits.
 // ---------------------------------------------------------------------------
-#define PPF_NOALLOC_PARTIALS_FLOATS (1 << 20)   // 4 MiB of partial sums
+#define PPF_NOALLOC_PARTIALS_FLOATS (1 << 19)   // 2 MiB of partial sums
 
 static __device__ __align__(256) float g_noalloc_partials[PPF_NOALLOC_PARTIALS_FLOATS];
 
@@ -577,7 +578,7 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
                                            long long n_streams, ppf_stream_t stream) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: invalid plan");
     if (!p->has_bwd)
-        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward_noalloc: needs complex FP32 input, C in [64, 256] and T <= 16");
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward_noalloc: needs C in [64, 512] with T <= 16 (T <= 8 at C = 512)");
     if (grad_out_dev == nullptr || in_dev == nullptr || (grad_in_dev == nullptr && grad_taps_dev == nullptr))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: NULL buffer");
     if (n_spectra < 1 || n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: empty problem");
@@ -588,7 +589,7 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     const long long n_raw = n_spectra + T - 1;
     const long long in_len = (long long)C * n_raw, out_len = (long long)C * n_spectra;
     if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), in_dev,
-                                (unsigned long long)(n_streams * in_len * 8)))
+                                (unsigned long long)(n_streams * in_len * bytes_in(p->in))))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward_noalloc: grad_in overlaps the input");
     // one row of TM*C partial sums per CTA; fewer CTAs per stream if the array is short
     const long long row = (long long)TM * C;
@@ -600,7 +601,7 @@ extern "C" ppf_status ppf_backward_noalloc(ppf_plan_t p, const void* grad_out_de
     const long long grid = std::min<long long>(work_units((long long)p->sms * p->bwd_occupancy, n_streams, nb), max_ctas);
     ppf::BwdArgs a;
     a.gY = static_cast<const float2*>(grad_out_dev);
-    a.x = static_cast<const float2*>(in_dev);
+    a.x = in_dev;
     a.taps = p->d_taps;
     a.tw = p->d_tw;
     a.gx = static_cast<float2*>(grad_in_dev);

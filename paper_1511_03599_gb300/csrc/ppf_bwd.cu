@@ -1,35 +1,47 @@
-// ppf_bwd.cu -- instantiates the PFB adjoint kernels (complex FP32 input,
-// C in {64, 128, 256}, tap buckets up to 16) and exports their lookup.
+// ppf_bwd.cu -- instantiates the PFB adjoint kernels (complex int8 / int16 /
+// FP32 input, C in {64, 128, 256, 512}, tap buckets up to 16 where the batch
+// holds the halo) and exports their lookup.
 #include "ppf_bwd.cuh"
 #include "ppf_internal.h"
 
 namespace ppf {
 
-template <int C, int TM>
+template <int C, int TM, int IN>
 static bool make_bwd(BwdEntry* e) {
-    const BwdInfo i = bwd_info<C, TM>();
+    const BwdInfo i = bwd_info<C, TM, IN>();
     if (i.fn == nullptr) return false;
-    *e = BwdEntry{i.threads, i.batch, i.smem, i.fn, &bwd_launch<C, TM>};
+    *e = BwdEntry{i.threads, i.batch, i.smem, i.fn, &bwd_launch<C, TM, IN>};
     return true;
 }
 
-template <int C>
+template <int C, int IN>
 static bool bwd_by_tm(int tm, BwdEntry* e) {
     switch (tm) {
-        case 1: return make_bwd<C, 1>(e);
-        case 2: return make_bwd<C, 2>(e);
-        case 4: return make_bwd<C, 4>(e);
-        case 8: return make_bwd<C, 8>(e);
-        case 16: return make_bwd<C, 16>(e);
+        case 1: return make_bwd<C, 1, IN>(e);
+        case 2: return make_bwd<C, 2, IN>(e);
+        case 4: return make_bwd<C, 4, IN>(e);
+        case 8: return make_bwd<C, 8, IN>(e);
+        case 16: return make_bwd<C, 16, IN>(e);
         default: return false;
     }
 }
 
-bool bwd_lookup(int C, int tm, BwdEntry* e) {
+template <int C>
+static bool bwd_by_in(int tm, int in, BwdEntry* e) {
+    switch (in) {
+        case IN_CI8: return bwd_by_tm<C, IN_CI8>(tm, e);
+        case IN_CI16: return bwd_by_tm<C, IN_CI16>(tm, e);
+        case IN_CF32: return bwd_by_tm<C, IN_CF32>(tm, e);
+        default: return false;
+    }
+}
+
+bool bwd_lookup(int C, int tm, int in, BwdEntry* e) {
     switch (C) {
-        case 64: return bwd_by_tm<64>(tm, e);
-        case 128: return bwd_by_tm<128>(tm, e);
-        case 256: return bwd_by_tm<256>(tm, e);
+        case 64: return bwd_by_in<64>(tm, in, e);
+        case 128: return bwd_by_in<128>(tm, in, e);
+        case 256: return bwd_by_in<256>(tm, in, e);
+        case 512: return bwd_by_in<512>(tm, in, e);
         default: return false;
     }
 }

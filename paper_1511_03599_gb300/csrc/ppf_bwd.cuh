@@ -30,22 +30,26 @@
 
 namespace ppf {
 
-template <int C, int TM>
+template <int C, int TM, int IN = IN_CF32>
 struct BwdShape {
     static constexpr int NT = C;                                     // one channel per thread
     static constexpr int B = 4096 / C;                               // raw rows per batch
-    static constexpr int SLOTB = B * C * 8;                          // complex FP32 rows of a batch
+    static constexpr int BIN = InTraits<IN>::bytes;
+    static constexpr int SLOTB = B * C * 8;                          // complex FP32 rows of G of a batch
+    static constexpr int XSLOTB = B * C * BIN;                       // raw rows of x of a batch
     static constexpr int NWARP = NT / 32;
-    static constexpr int SPW = NWARP > 0 ? B / NWARP : 0;            // spectra per warp in the DFT
+    // spectra per warp in the inverse DFT; 0: the stages are spread over the
+    // whole CTA (C = 512, where a batch has fewer spectra than warps)
+    static constexpr int SPW = NWARP > 0 && B >= NWARP ? B / NWARP : 0;
     static constexpr int TWB = tw_size(C) * 8;                       // twiddle tables
-    static constexpr int SMEM = 4 * SLOTB + TWB + 64;                // G slots, x slots, twiddles, barriers
-    static constexpr bool OK = (C >= 64 && C <= 256) && (TM <= 16) && (B >= TM - 1) &&
-                               SPW >= 1 && SPW * NWARP == B && fft_items_fit(C, SPW, 32);
+    static constexpr int SMEM = 2 * SLOTB + 2 * XSLOTB + TWB + 64;   // G slots, x slots, twiddles, barriers
+    static constexpr bool FFT_OK = SPW > 0 ? (SPW * NWARP == B && fft_items_fit(C, SPW, 32)) : C == 512;
+    static constexpr bool OK = (C >= 64 && C <= 512) && (TM <= 16) && (B >= TM - 1) && FFT_OK;
 };
 
 struct BwdArgs {
     const float2* gY;        // incoming gradient, n_spectra*C per stream
-    const float2* x;         // forward input, C*(n_spectra+T-1) per stream
+    const void* x;           // forward input (the plan's input type), C*(n_spectra+T-1) samples per stream
     const float* taps;       // TM*C floats, tap-major, rows >= T zero
     const float2* tw;        // twiddle tables of the forward plan
     float2* gx;              // grad wrt x, same layout as x (nullptr: skip)
@@ -58,16 +62,16 @@ struct BwdArgs {
     int flags;
 };
 
-template <int C, int TM>
-__global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs args) {
-    using S = BwdShape<C, TM>;
-    constexpr int NT = S::NT, B = S::B, NST = fft_stages(C);
+template <int C, int TM, int IN>
+__global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(BwdArgs args) {
+    using S = BwdShape<C, TM, IN>;
+    constexpr int NT = S::NT, B = S::B, NST = fft_stages(C), BIN = S::BIN;
     static_assert(S::OK, "shape not supported by the backward kernel");
     extern __shared__ __align__(128) unsigned char smem[];
-    float2* gslot = reinterpret_cast<float2*>(smem);                    // [2][B][C]
-    float2* xslot = reinterpret_cast<float2*>(smem + 2 * S::SLOTB);     // [2][B][C]
-    float2* tw_s = reinterpret_cast<float2*>(smem + 4 * S::SLOTB);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 4 * S::SLOTB + S::TWB);  // g0 g1 x0 x1 never
+    float2* gslot = reinterpret_cast<float2*>(smem);                    // [2][B][C] complex FP32
+    unsigned char* xslot = smem + 2 * S::SLOTB;                         // [2][B][C] raw samples
+    float2* tw_s = reinterpret_cast<float2*>(smem + 2 * S::SLOTB + 2 * S::XSLOTB);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * S::SLOTB + 2 * S::XSLOTB + S::TWB);  // g0 g1 x0 x1 never
     volatile int* sflag = reinterpret_cast<volatile int*>(bars + 5);
 
     const int c = threadIdx.x;
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         u = strm * nbt + hi;
         const long long nb = hi - lo;
         const float2* gY = args.gY + (size_t)strm * args.gY_stride;
-        const float2* x = args.x + (size_t)strm * args.x_stride;
+        const unsigned char* x = static_cast<const unsigned char*>(args.x) + (size_t)strm * args.x_stride * BIN;
         float2* gx = args.gx ? args.gx + (size_t)strm * args.x_stride : nullptr;
 
         unsigned long long carry[TM > 1 ? TM - 1 : 1];     // g_y rows (first row) - (TM-1) .. -1
@@ -138,9 +142,10 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
             if (k >= 0) {
                 const long long xr = x_rows(j);
                 const int qx = (int)((xbase + k) & 1);
-                mbar_expect_tx(&bars[2 + qx], (uint32_t)(xr * C * 8));
+                mbar_expect_tx(&bars[2 + qx], (uint32_t)(xr * C * BIN));
                 if (xr > 0)
-                    tma_load_1d(xslot + qx * B * C, x + (size_t)j * B * C, (uint32_t)(xr * C * 8), &bars[2 + qx]);
+                    tma_load_1d(xslot + qx * S::XSLOTB, x + (size_t)j * B * C * BIN, (uint32_t)(xr * C * BIN),
+                                &bars[2 + qx]);
             }
         };
         auto wait_it = [&](long long it, uint64_t limit) -> bool {
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
         for (long long it = 0; it < nit; ++it) {
             const long long k = it + k0, j = lo + k;
             float2* gs = gslot + ((gbase + it) & 1) * B * C;
-            const float2* xs = xslot + ((xbase + k) & 1) * B * C;
+            const unsigned char* xs = xslot + ((xbase + k) & 1) * S::XSLOTB;
             if (c == 0) {
                 bool ok = wait_it(it, kWaitLimitNs);
                 if (gbase == 0 && it == 0 && (args.flags & FWD_INJECT_TIMEOUT))
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
 #pragma unroll
             for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
             const float2* gsc = gs + c;
-            const float2* xsc = xs + c;
+            const unsigned char* xsc = xs + c * BIN;
             if (row0 + B <= n_spectra && T == TM) {        // whole batch, every tap: no checks
 #pragma unroll
                 for (int r = 0; r < B; ++r) {
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
                 if (k >= 0) {
 #pragma unroll
                     for (int r = 0; r < B; ++r) {
-                        const float2 xv = xsc[r * C];
+                        const float2 xv = load_one_smem<IN>(xsc + (size_t)r * C * BIN);
                         const unsigned long long xp = pk2(xv.x, xv.y);
 #pragma unroll
                         for (int t = 0; t < TM; ++t) {
@@ -220,7 +225,8 @@ __global__ void __launch_bounds__(BwdShape<C, TM>::NT, 1) pfb_bwd_kernel(BwdArgs
                 if (k >= 0) {
 #pragma unroll
                     for (int r = 0; r < B; ++r) {
-                        const float2 xv = (row0 + r < n_raw) ? xsc[r * C] : make_float2(0.f, 0.f);
+                        const float2 xv = (row0 + r < n_raw) ? load_one_smem<IN>(xsc + (size_t)r * C * BIN)
+                                                             : make_float2(0.f, 0.f);
                         const unsigned long long xp = pk2(xv.x, xv.y);
 #pragma unroll
                         for (int t = 0; t < TM; ++t) {
@@ -279,18 +285,18 @@ struct BwdInfo {
     const void* fn;
 };
 
-template <int C, int TM>
+template <int C, int TM, int IN>
 inline BwdInfo bwd_info() {
-    using S = BwdShape<C, TM>;
-    if constexpr (S::OK) return BwdInfo{S::NT, S::B, S::SMEM, reinterpret_cast<const void*>(&pfb_bwd_kernel<C, TM>)};
+    using S = BwdShape<C, TM, IN>;
+    if constexpr (S::OK) return BwdInfo{S::NT, S::B, S::SMEM, reinterpret_cast<const void*>(&pfb_bwd_kernel<C, TM, IN>)};
     else return BwdInfo{0, 0, 0, nullptr};
 }
 
-template <int C, int TM>
+template <int C, int TM, int IN>
 inline cudaError_t bwd_launch(const BwdArgs& a, int grid, cudaStream_t st) {
-    using S = BwdShape<C, TM>;
+    using S = BwdShape<C, TM, IN>;
     if constexpr (S::OK) {
-        pfb_bwd_kernel<C, TM><<<grid, S::NT, S::SMEM, st>>>(a);
+        pfb_bwd_kernel<C, TM, IN><<<grid, S::NT, S::SMEM, st>>>(a);
         return cudaPeekAtLastError();
     } else {
         return cudaErrorNotSupported;

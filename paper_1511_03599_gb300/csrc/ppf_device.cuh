@@ -259,13 +259,18 @@ __device__ __forceinline__ void ffma2(unsigned long long& d, unsigned long long 
 }
 
 // ---------------------------------------------------------------- stores
+#ifndef PPF_STORE_CS
+#define PPF_STORE_CS 1
+#endif
 template <int OUT>
 __device__ __forceinline__ void store_out(void* __restrict__ base, long long idx, float2 v) {
     if constexpr (OUT == OUT_CF32) {
-        __stcs(reinterpret_cast<float2*>(base) + idx, v);
+        if constexpr (PPF_STORE_CS) __stcs(reinterpret_cast<float2*>(base) + idx, v);
+        else reinterpret_cast<float2*>(base)[idx] = v;
     } else {
         __half2 h = __float22half2_rn(v);
-        __stcs(reinterpret_cast<unsigned int*>(base) + idx, *reinterpret_cast<unsigned int*>(&h));
+        if constexpr (PPF_STORE_CS) __stcs(reinterpret_cast<unsigned int*>(base) + idx, *reinterpret_cast<unsigned int*>(&h));
+        else reinterpret_cast<unsigned int*>(base)[idx] = *reinterpret_cast<unsigned int*>(&h);
     }
 }
 

@@ -121,12 +121,15 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 }
 
 // ------------------------------------------------------------ launch shape
+#ifndef PPF_GENERIC_B4096
+#define PPF_GENERIC_B4096 2      // spectra per batch of the generic kernel at C = 4096
+#endif
 template <int C, int TM, int IN, int NTO = 0>
 struct FwdShape {
     static constexpr int NT = NTO ? NTO : (C >= 2048 ? 512 : 256);   // threads per CTA
     static constexpr int PAIRS = C / 2;
     // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k)
-    static constexpr int B = (C >= 4096) ? 2 : (C >= 2048) ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
+    static constexpr int B = (C >= 4096) ? PPF_GENERIC_B4096 : (C >= 2048) ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
     // large-T FIR order (see fir_segment): tap chunks for narrow input at C <= 512
     static constexpr bool CHUNK = TM > 16 && IN != IN_CF32 && C <= 512;
     static constexpr int L0 = (TM >= 32 && !CHUNK) ? 8 : 16;
@@ -139,11 +142,14 @@ struct FwdShape {
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BIN = InTraits<IN>::bytes;
     static constexpr int SLOTB = B * C * BIN;                        // raw bytes of one batch
-    static constexpr int NS = 3;                                     // ring slots
     static constexpr int CTA_SMEM_MAX = (NT == 256 ? 113 * 1024 : 226 * 1024) - 128;
     // TMA ring: every raw batch is copied into shared memory once; the FIR of
-    // batch k reads slot k and the T-1 halo rows at the head of slot k+1.
-    static constexpr bool RING = (TM - 1 <= B) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
+    // batch k reads slot k and the T-1 halo rows from the HS slots after it
+    // (HS = 1 when T-1 <= B; a deeper ring where the halo spans several
+    // batches -- large C, where B is small -- and one segment covers the batch).
+    static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
+    static constexpr int NS = HS + 2;                                // ring slots
+    static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
     static constexpr bool TW_SMEM = YBYTES + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
     static constexpr int SMEM = RING_OFF + (RING ? NS * SLOTB + 64 : 0);
@@ -173,6 +179,22 @@ struct FwdArgs {
     int flags;               // FwdFlags (testing aid)
 };
 
+// Thread-group policies: which threads run a body and how they synchronise.
+// CtaGroup: the whole CTA (__syncthreads).  HalfGroup<N>: threads
+// [g*N, g*N + N) form group g and synchronise on named barrier g + 1, so the
+// groups of one CTA run independent bodies (the multi-beam kernel).
+struct CtaGroup {
+    __device__ static __forceinline__ int tid() { return threadIdx.x; }
+    __device__ static __forceinline__ void sync() { __syncthreads(); }
+};
+template <int N>
+struct HalfGroup {
+    __device__ static __forceinline__ int tid() { return threadIdx.x % N; }
+    __device__ static __forceinline__ void sync() {
+        asm volatile("bar.sync %0, %1;" ::"r"((int)(threadIdx.x / N) + 1), "n"(N) : "memory");
+    }
+};
+
 // One FFT stage over the whole batch held in shared memory.
 // Output spectrum of batch row sp is sb + sp; it is stored when it lies in [vlo, vhi).
 // SPW > 0: warp-local mode, warp w owns batch rows [w*SPW, (w+1)*SPW) in every
@@ -182,7 +204,7 @@ struct FwdArgs {
 // its last stage writes the result back into the spectrum's own row of
 // ybuf in natural order instead of to global memory.
 template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false, bool SMEM_OUT = false,
-          int LAYOUT = 0>
+          int LAYOUT = 0, class GRP = CtaGroup>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
                                           void* __restrict__ out, long long sb, long long vlo, long long vhi) {
     constexpr int NST = fft_stages(C);
@@ -199,11 +221,12 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     static_assert(!(LAYOUT == 1 && (INV || SMEM_OUT)), "padded rows only for the forward stores to HBM");
     static_assert(EXACT || (SPW == 0 && is_c3(C)) || TOTAL < WORKERS,
                   "items must divide evenly (a warp or CTA may leave threads idle)");
-    const int wid = SPW > 0 ? (threadIdx.x & 31) : threadIdx.x;
-    const int sp0 = SPW > 0 ? (threadIdx.x >> 5) * SPW : 0;
+    const int gtid = GRP::tid();
+    const int wid = SPW > 0 ? (gtid & 31) : gtid;
+    const int sp0 = SPW > 0 ? (gtid >> 5) * SPW : 0;
     auto sync = [] {
         if constexpr (SPW > 0) __syncwarp();
-        else __syncthreads();
+        else GRP::sync();
     };
 
     float2 v[IPT][R];
@@ -257,21 +280,14 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     if constexpr (P + 1 < NST || INV) sync();
 }
 
-__device__ __forceinline__ void fma_pair(float4& acc, float2 h, float4 x) {
-    acc.x = fmaf(h.x, x.x, acc.x);
-    acc.y = fmaf(h.x, x.y, acc.y);
-    acc.z = fmaf(h.y, x.z, acc.z);
-    acc.w = fmaf(h.y, x.w, acc.w);
-}
-
 // Where the FIR reads raw samples of channel pair cp from: rows are relative
 // to the first raw spectrum of the batch (row r feeds outputs r-T+1 .. r).
-template <int C, int IN, bool RING, int B>
+template <int C, int IN, bool RING, int B, int HS = 1>
 struct RawSrc {
     static constexpr int BIN = InTraits<IN>::bytes;
-    // ring: shared-memory slots of the batch and of the next batch
-    const unsigned char* cur;
-    const unsigned char* nxt;
+    static constexpr bool kRing = RING;
+    // ring: shared-memory slots of the batch and of the HS batches after it
+    const unsigned char* sl[HS + 1];
     // direct: global stream
     const void* in;
     long long row0, n_raw;
@@ -279,8 +295,12 @@ struct RawSrc {
 
     __device__ __forceinline__ float4 load(int r) const {
         if constexpr (RING) {
-            const unsigned char* p = (r < B) ? cur + (size_t)r * C * BIN : nxt + (size_t)(r - B) * C * BIN;
-            return load_pair_smem<IN>(p);
+            if constexpr (HS == 1) {
+                const unsigned char* p = (r < B) ? sl[0] + (size_t)r * C * BIN : sl[1] + (size_t)(r - B) * C * BIN;
+                return load_pair_smem<IN>(p);
+            } else {
+                return load_pair_smem<IN>(sl[r / B] + (size_t)(r % B) * C * BIN);   // r is a compile-time row here
+            }
         } else {
             const long long rr = row0 + r;
             return (rr < n_raw) ? load_pair_global<IN>(in, rr * C + 2 * cp) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -297,6 +317,13 @@ struct RawSrc {
     }
 };
 
+__device__ __forceinline__ void fma_pair(float4& acc, float2 h, float4 x) {
+    acc.x = fmaf(h.x, x.x, acc.x);
+    acc.y = fmaf(h.x, x.y, acc.y);
+    acc.z = fmaf(h.y, x.z, acc.z);
+    acc.w = fmaf(h.y, x.w, acc.w);
+}
+
 // FIR (Alg. 1) of channel pair cp for the L output spectra whose first raw
 // row is r0 (relative to the batch):
 //   acc[j] = sum_{t<T} h[t][cp] * x[r0 + j + t][cp]
@@ -308,15 +335,16 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
                                             int T, float4 (&acc)[L]) {
 #pragma unroll
     for (int j = 0; j < L; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (TM <= 16) {
-        // raw-sample-outer order: all TM taps live in registers, one sample live.
+    if constexpr (TM <= 16 && !(Src::kRing && IN != IN_CF32 && L >= 4)) {
+        // raw-sample-outer order: all TM taps live in registers, one sample live
+        // (scalar FMAs: faster than the packed form below when the samples come
+        // from global memory, for fp32 samples and for segments of 2 outputs)
         float2 h[TM];
 #pragma unroll
         for (int t = 0; t < TM; ++t) {
             if constexpr (TAPS_IN_REGS) h[t] = hreg[t];
             else h[t] = __ldg(taps2 + t * PAIRS + cp);
         }
-        // a segment wholly inside the stream loads without per-sample bounds checks
         auto run = [&](auto inside_tag) {
             constexpr bool INSIDE = decltype(inside_tag)::value != 0;
 #pragma unroll
@@ -339,6 +367,47 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
         };
         if (src.inside(r0, L + T - 1)) run(ic<1>{});
         else run(ic<0>{});
+    } else if constexpr (TM <= 16) {
+        // samples staged in shared memory, 8/16-bit input, segments of >= 4
+        // outputs: packed FMAs on channel pairs -- accumulators (re0, re1) and (im0, im1), taps
+        // (h[2cp], h[2cp+1]) as loaded, samples converted straight into pairs
+        unsigned long long hp[TM];
+#pragma unroll
+        for (int t = 0; t < TM; ++t) {
+            const float2 h = TAPS_IN_REGS ? hreg[t < (TAPS_IN_REGS ? TM : 1) ? t : 0] : __ldg(taps2 + t * PAIRS + cp);
+            hp[t] = pk2(h.x, h.y);
+        }
+        unsigned long long ar[L], ai[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) ar[j] = ai[j] = 0ull;
+        // a segment wholly inside the stream loads without per-sample bounds checks
+        auto run = [&](auto inside_tag) {
+            constexpr bool INSIDE = decltype(inside_tag)::value != 0;
+#pragma unroll
+            for (int i = 0; i < L + TM - 1; ++i) {
+                if (i < L + T - 1) {
+                    const float4 x = INSIDE ? src.load_inside(r0 + i) : src.load(r0 + i);
+                    const unsigned long long xr = pk2(x.x, x.z), xi = pk2(x.y, x.w);
+#pragma unroll
+                    for (int j = 0; j < L; ++j) {
+                        const int t = i - j;
+                        if (t >= 0 && t < TM) {
+                            if (IN != IN_CF32 || t < T) {     // fp32: keep inf/NaN out of unrelated outputs
+                                ffma2(ar[j], hp[t], xr);       // taps t >= T are zero
+                                ffma2(ai[j], hp[t], xi);
+                            }
+                        }
+                    }
+                }
+            }
+        };
+        if (src.inside(r0, L + T - 1)) run(ic<1>{});
+        else run(ic<0>{});
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const float2 a = upk2(ar[j]), b = upk2(ai[j]);
+            acc[j] = make_float4(a.x, b.x, a.y, b.y);
+        }
     } else {
         // Large T (T is a runtime bound); packed (re, im) x (h, h) FMAs; a
         // segment wholly inside the stream loads without per-sample bounds
@@ -424,7 +493,7 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
 // offset to the stream), by the whole CTA, using `smem`.  Returns false when
 // a bounded wait gave up (the status word is then set).  Safe to call again
 // for another range (the tile loop of the multi-beam kernel).
-template <int C, int TM, int IN, int OUT, int NTO = 0>
+template <int C, int TM, int IN, int OUT, int NTO = 0, class GRP = CtaGroup>
 __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, void* out, long long lo,
                                           long long hi, unsigned char* smem) {
     using S = FwdShape<C, TM, IN, NTO>;
@@ -437,13 +506,13 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NS * S::SLOTB);   // NS + 1 barriers
     volatile int* sflag = reinterpret_cast<volatile int*>(bars + NS + 1);
 
-    const int tid = threadIdx.x;
+    const int tid = GRP::tid();
     const long long n_spectra = args.n_spectra;
     const int T = args.T;
     const long long n_raw = n_spectra + T - 1;
     const long long nb = hi - lo;
     if (nb <= 0) return true;
-    __syncthreads();   // the previous range of this CTA is done with shared memory
+    GRP::sync();   // the previous range of this CTA is done with shared memory
     const float2* tws = args.tw;
     if constexpr (S::TW_SMEM) {
         for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
@@ -463,7 +532,9 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
         const long long r = n_raw - (lo + j) * B;
         return r <= 0 ? 0 : (r < B ? r : B);
     };
-    const long long last_needed = (T > 1) ? nb : nb - 1;   // last relative batch the FIRs read
+    // last relative batch the FIRs read: the halo of the range's last batch
+    // ends in batch nb-1 + ceil((T-1)/B) (rows past the stream are not copied)
+    const long long last_needed = nb - 1 + (T - 1 + B - 1) / B;
     long long issued = 0, waited = 0;                        // meaningful in thread 0 only
     auto issue = [&](long long j) {
         const long long rows = rows_of(j);
@@ -489,19 +560,19 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
             fence_mbar_init();
             *sflag = 0;
         }
-        __syncthreads();
+        GRP::sync();
         if (tid == 0) {
             fence_proxy_async_smem();   // the slots were last read by the previous range's FIR
             for (; issued < NS && issued <= last_needed; ++issued) issue(issued);
         }
     }
-    __syncthreads();
+    GRP::sync();
 
     for (long long k = 0; k < nb; ++k) {
         const long long sb = (lo + k) * B;          // first output spectrum of the batch
         if constexpr (RING) {
             if (tid == 0) {
-                bool ok = wait_upto((T > 1) ? k + 1 : k);
+                bool ok = wait_upto(k + (T - 1 + B - 1) / B);
                 if (k == 0 && (args.flags & FWD_INJECT_TIMEOUT))  // a barrier nothing arrives on
                     ok = ok && mbar_wait_bounded(&bars[NS], 0, kInjectedWaitNs);
                 if (!ok) {
@@ -513,7 +584,7 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
                     *sflag = 1;
                 }
             }
-            __syncthreads();
+            GRP::sync();
             if (*sflag) return false;
         } else {
             if (tid == 0 && k + 2 < nb) {           // warm L2 two batches ahead
@@ -529,10 +600,10 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
             const int item = tid + f * NT;
             if (!S::FIR_EXACT && item >= S::FIR_ITEMS) break;
             const int cp = item % S::PAIRS, g = item / S::PAIRS;
-            RawSrc<C, IN, RING, B> src;
+            RawSrc<C, IN, RING, B, S::HS> src;
             if constexpr (RING) {
-                src.cur = ring + (k % NS) * S::SLOTB + 2 * cp * S::BIN;
-                src.nxt = ring + ((k + 1) % NS) * S::SLOTB + 2 * cp * S::BIN;
+#pragma unroll
+                for (int h = 0; h <= S::HS; ++h) src.sl[h] = ring + ((k + h) % NS) * S::SLOTB + 2 * cp * S::BIN;
             } else {
                 src.in = in;
                 src.row0 = sb;
@@ -540,12 +611,13 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
                 src.cp = cp;
             }
             float4 acc[L];
-            fir_segment<TM, IN, L, S::PAIRS, S::TAPS_IN_REGS, S::CHUNK>(src, taps2, hreg, cp, g * L, T, acc);
+            fir_segment<TM, IN, L, S::PAIRS, S::TAPS_IN_REGS, S::CHUNK>(src, taps2, hreg, cp, S::G == 1 ? 0 : g * L,
+                                                                        T, acc);
 #pragma unroll
             for (int j = 0; j < L; ++j)
                 *reinterpret_cast<float4*>(ybuf + (g * L + j) * C + 2 * cp) = acc[j];
         }
-        __syncthreads();
+        GRP::sync();
         if constexpr (RING) {
             // slot k is free: refill it with batch k+NS
             if (tid == 0 && issued <= last_needed && issued == k + NS) {
@@ -556,7 +628,8 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
         }
         // ---------------------------------------------------------- FFT
         static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM>(ybuf, tws, out, sb, 0, n_spectra);
+            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, 0, false, false, 0, GRP>(ybuf, tws, out, sb, 0,
+                                                                                              n_spectra);
         });
     }
     if constexpr (RING) {
@@ -616,15 +689,16 @@ struct FwdInfo {
 #include "ppf_fwd_push.cuh"
 #include "ppf_fwd_longtap.cuh"
 
-// Selection switches for the push-exchange cluster kernel (C = 2048/4096,
-// int8) and the long-tap kernel (T = 17..64, C <= 512): both pass every
-// parity test but measured slower than the generic and cluster kernels they
-// would replace, so they are compiled only when enabled.
+// Selection switches.  The push-exchange cluster kernel (C = 2048/4096, int8)
+// passes every parity test but measured slower than the cluster and generic
+// kernels it would replace, so it is compiled only when enabled.  The
+// long-tap kernel (T = 17..64, C <= 512) is the default for those shapes
+// (1.1 - 1.7x the generic kernel).
 #ifndef PPF_NO_PUSH
 #define PPF_NO_PUSH 1
 #endif
 #ifndef PPF_NO_LONGTAP
-#define PPF_NO_LONGTAP 1
+#define PPF_NO_LONGTAP 0
 #endif
 
 namespace ppf {
@@ -703,6 +777,9 @@ inline cudaError_t fir_launch(const FwdArgs& a, int grid, cudaStream_t st) {
 // Twiddle table contents (host, FP64 -> FP32): stage p < P-1 holds
 // W_{N_p}^{b k} = exp(-2 pi i b k / N_p), k = 1 .. R_p-1, at
 // [tw_offset(p) + (k-1)*N_{p+1} + b].
+// Entries of the plan's twiddle table for C.
+constexpr int tw_total_float2s(int C) { return tw_size(C); }
+
 template <int C>
 inline void fill_twiddles(float2* host) {
     for (int p = 0; p + 1 < fft_stages(C); ++p) {

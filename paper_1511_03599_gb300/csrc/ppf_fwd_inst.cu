@@ -81,7 +81,7 @@ bool PPF_CAT(fir_lookup_c, PPF_C)(int tm, int in, FwdEntry* e) {
     }
 }
 
-int PPF_CAT(fwd_twiddle_count_c, PPF_C)() { return tw_size(PPF_C) > 0 ? tw_size(PPF_C) : 1; }
+int PPF_CAT(fwd_twiddle_count_c, PPF_C)() { return tw_total_float2s(PPF_C) > 0 ? tw_total_float2s(PPF_C) : 1; }
 
 void PPF_CAT(fwd_twiddles_c, PPF_C)(float* host_pairs) {
     fill_twiddles<PPF_C>(reinterpret_cast<float2*>(host_pairs));

@@ -123,16 +123,17 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
             issue(issued);
         }
     };
-    auto wait_full = [&](long long g) {         // every thread: chunk use g has landed
+    // every thread: the chunk in `slot` (phase parity `par`) has landed
+    auto wait_full = [&](int slot, int par) {
         if (*sdead) return;
-        if (!mbar_wait_bounded(&full[g % NS], (uint32_t)((g / NS) & 1), kWaitLimitNs)) {
+        if (!mbar_wait_bounded(&full[slot], (uint32_t)par, kWaitLimitNs)) {
             atomicExch(args.err, 1);
             *sdead = 1;
         }
     };
-    auto release = [&](long long g) {           // every thread: done with chunk use g
+    auto release = [&](int slot) {              // every thread: done with the chunk in `slot`
         __syncwarp();
-        if (lane == 0) mbar_arrive_cta(&empty[g % NS]);
+        if (lane == 0) mbar_arrive_cta(&empty[slot]);
     };
 
     BatchShare share(nbt, args.n_streams, blockIdx.x, gridDim.x);
@@ -155,54 +156,89 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
 
         for (long long k = lo; k < hi; ++k) {
             const long long g0 = g_base + (k - lo) * nch;      // first chunk use of this batch
+            const int s0 = (int)(g0 % NS), q0 = (int)((g0 / NS) & 1);
+            // slot and phase parity of chunk c of this batch (chunk use g0 + c)
+            auto slot_of = [&](int c) { return (s0 + c) % NS; };
+            auto par_of = [&](int c) { return (q0 + (s0 + c) / NS) & 1; };
             // ------------------------------------------------------------- FIR
+            // channel-paired accumulators: acc[j][0] = (re, re), acc[j][1] = (im, im) of
+            // channels (2cp, 2cp+1) for output j; window rows likewise as (re, re), (im, im)
+            // pairs, and each tap is used as loaded, (h[2cp], h[2cp+1])
             unsigned long long acc[B][2];
 #pragma unroll
             for (int j = 0; j < B; ++j) acc[j][0] = acc[j][1] = 0ull;
-            float4 xw[B];
+            unsigned long long xr[B], xi[B];
+            auto load_row = [&](const unsigned char* p, int i) {
+                const float4 v = load_pair_smem<IN>(p);
+                xr[i] = pk2(v.x, v.z);
+                xi[i] = pk2(v.y, v.w);
+            };
             // rows 0 .. B-1 of the batch fill the window (B / RC whole chunks)
 #pragma unroll
             for (int c = 0; c < B / RC; ++c) {
-                wait_full(g0 + c);
-                const unsigned char* slot = ring + (int)((g0 + c) % NS) * S::CHUNKB + 2 * cp * BIN;
+                const int sl = slot_of(c);
+                wait_full(sl, par_of(c));
+                const unsigned char* src = ring + sl * S::CHUNKB + 2 * cp * BIN;
 #pragma unroll
-                for (int i = 0; i < RC; ++i) xw[c * RC + i] = load_pair_smem<IN>(slot + (size_t)i * C * BIN);
-                release(g0 + c);
+                for (int i = 0; i < RC; ++i) load_row(src + (size_t)i * C * BIN, c * RC + i);
+                release(sl);
                 if (tid == 0 && !*sdead) refill(g0 + c + 1 + NS);
             }
+            // taps 4 ahead in a rolling set of registers (tap t lives in hq[t % 4]); the
+            // plan pads the tap table with zero rows, so loads past T stay in bounds
+            const float2* tp = taps2 + cp;
+            unsigned long long hq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 h = __ldg(tp + i * (C / 2));
+                hq[i] = pk2(h.x, h.y);
+            }
             // taps in blocks of B: tap t = tb + u uses window slot (j + u) mod B for output j,
-            // then slot u takes row t + B (chunk (t + B) / RC)
-            for (int tb = 0; tb < T; tb += B) {
+            // then slot u takes row t + B, in chunk (t + B) / RC, at row (t + B) mod RC = u mod RC.
+            // FULL: every tap of the block exists and every row it loads lies in the batch
+            // (tb + B <= T - 1), so the block runs without per-tap checks.
+            auto block = [&](int tb, auto full_tag) {
+                constexpr bool FULL = decltype(full_tag)::value != 0;
+                int csl[B / RC];
+                const unsigned char* csrc[B / RC];
+#pragma unroll
+                for (int h = 0; h < B / RC; ++h) {
+                    const int c = (tb + B) / RC + h;
+                    csl[h] = slot_of(c);
+                    csrc[h] = ring + csl[h] * S::CHUNKB + 2 * cp * BIN;
+                    if (FULL || tb + h * RC < T - 1) wait_full(csl[h], par_of(c));
+                }
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
                     const int t = tb + u;
-                    if (t < T) {
-                        const float2 h = __ldg(taps2 + t * (C / 2) + cp);
-                        const unsigned long long h0 = pk2(h.x, h.x), h1 = pk2(h.y, h.y);
+                    if (FULL || t < T) {
+                        const unsigned long long h = hq[u % 4];
+                        {
+                            const float2 hn = __ldg(tp + (t + 4) * (C / 2));
+                            hq[u % 4] = pk2(hn.x, hn.y);
+                        }
 #pragma unroll
                         for (int j = 0; j < B; ++j) {
-                            const float4 x = xw[(j + u) % B];
-                            ffma2(acc[j][0], h0, pk2(x.x, x.y));
-                            ffma2(acc[j][1], h1, pk2(x.z, x.w));
+                            ffma2(acc[j][0], h, xr[(j + u) % B]);
+                            ffma2(acc[j][1], h, xi[(j + u) % B]);
                         }
-                        const int r = t + B;                    // the row that takes slot u
-                        if (r < B + T - 1) {
-                            const long long g = g0 + r / RC;
-                            if (u % RC == 0) wait_full(g);      // r % RC == u % RC (B and tb are multiples of RC)
-                            xw[u] = load_pair_smem<IN>(ring + (int)(g % NS) * S::CHUNKB + 2 * cp * BIN +
-                                                       (size_t)(u % RC) * C * BIN);
-                            if (u % RC == RC - 1 || r == B + T - 2) {
-                                release(g);
-                                if (tid == 0 && !*sdead) refill(g + 1 + NS);
+                        if (FULL || t < T - 1) {                // row t + B exists in the batch
+                            load_row(csrc[u / RC] + (size_t)(u % RC) * C * BIN, u);
+                            if (u % RC == RC - 1 || (!FULL && t == T - 2)) {
+                                release(csl[u / RC]);
+                                if (tid == 0 && !*sdead) refill(g0 + (tb + B) / RC + u / RC + 1 + NS);
                             }
                         }
                     }
                 }
-            }
+            };
+            int tb = 0;
+            for (; tb + B <= T - 1; tb += B) block(tb, ic<1>{});
+            for (; tb < T; tb += B) block(tb, ic<0>{});
 #pragma unroll
             for (int j = 0; j < B; ++j) {
-                const float2 a = upk2(acc[j][0]), b2 = upk2(acc[j][1]);
-                *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(a.x, a.y, b2.x, b2.y);
+                const float2 r = upk2(acc[j][0]), im = upk2(acc[j][1]);
+                *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(r.x, im.x, r.y, im.y);
             }
             __syncthreads();
             // ------------------------------------------------------------- FFT

@@ -39,8 +39,8 @@ struct BwdEntry {
     const void* fn;
     cudaError_t (*launch)(const BwdArgs&, int grid, cudaStream_t);
 };
-// Adjoint kernels (complex FP32 input only); false when (C, tap bucket) is not built.
-bool bwd_lookup(int C, int tap_bucket, BwdEntry* e);
+// Adjoint kernels; false when (C, tap bucket, input type) is not built.
+bool bwd_lookup(int C, int tap_bucket, int in, BwdEntry* e);
 // grad_h[t*C + c] = sum_p partials[p*TM*C + t*C + c], p in order (NaN when *err != 0).
 cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, const int* err, float* grad_h,
                        cudaStream_t st);

@@ -213,19 +213,30 @@ class Plan:
     def backward(self, grad_out, x, want_input: bool = True, want_taps: bool = True, stream=None):
         """Adjoint: (grad wrt x or None, grad wrt taps (C*T float32) or None).
 
-        grad_out: complex64 CUDA tensor (..., S, C); x: the forward input (complex64,
-        or float32 interleaved), with the same leading stream dimension if any.
+        grad_out: complex64 CUDA tensor (..., S, C); x: the forward input in the
+        plan's input type (complex64 / interleaved float32, int16 or int8), with the
+        same leading stream dimension if any.  The input gradient is complex64,
+        one value per input sample, shaped like x (complex) or like x with the
+        interleaved real/imaginary axis folded (real-pair inputs).
         """
         import torch
-        if self.in_dtype != "cf32":
-            raise TypeError("backward() needs a complex FP32 input plan")
         if not (grad_out.is_cuda and x.is_cuda) or grad_out.dtype != torch.complex64:
-            raise TypeError("backward() takes complex64 CUDA tensors")
+            raise TypeError("backward() takes a complex64 CUDA gradient and a CUDA input")
+        self._check_input(x)
         grad_out = grad_out.contiguous()
         x = x.contiguous()
         S = grad_out.shape[-2]
         ns = grad_out.numel() // (S * self.C)
-        gx = torch.empty_like(x) if want_input else None
+        n_samples = x.numel() if x.is_complex() else x.numel() // 2
+        if n_samples != ns * self.C * (S + self.T - 1):
+            raise ValueError("x does not hold n_streams * C * (S + T - 1) samples")
+        if x.is_complex():
+            gx_shape = tuple(x.shape)
+        elif x.dim() >= 2 and x.shape[-1] == 2:
+            gx_shape = tuple(x.shape[:-1])          # (..., 2) real/imag pairs
+        else:
+            gx_shape = tuple(x.shape[:-1]) + (x.shape[-1] // 2,)   # interleaved along the last axis
+        gx = torch.empty(gx_shape, dtype=torch.complex64, device=x.device) if want_input else None
         gh = torch.empty(self.C * self.T, dtype=torch.float32, device=x.device) if want_taps else None
         check(lib().ppf_backward(self.handle, ctypes.c_void_p(grad_out.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                  ctypes.c_void_p(gx.data_ptr() if gx is not None else 0),

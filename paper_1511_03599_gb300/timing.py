@@ -1,7 +1,7 @@
 """Time one forward or adjoint case of the C ABI with CUDA events.
 
     python -m paper_1511_03599_gb300.timing forward C T IN [OUT] [--spectra S] [--streams N]
-    python -m paper_1511_03599_gb300.timing backward C T [--spectra S] [--streams N]
+    python -m paper_1511_03599_gb300.timing backward C T [IN] [--spectra S] [--streams N]
 
 Inputs are the seeded synthetic streams of ``synth`` (drawn on the device);
 the default spectrum count gives 2^28 samples per stream, above the L2 size.
@@ -49,18 +49,21 @@ def forward(C: int, T: int, in_dtype: str, out_dtype: str, S: int, n_streams: in
             "GB_s": n_streams * b / ms / 1e6, "launch": info}
 
 
-def backward(C: int, T: int, S: int, n_streams: int, warmup: int, reps: int) -> dict:
+def backward(C: int, T: int, in_dtype: str, S: int, n_streams: int, warmup: int, reps: int) -> dict:
     import torch
     from . import ppf, synth
     g = torch.Generator(device="cuda")
     g.manual_seed(synth.SEED_BASE + 20)
-    x = torch.randn((n_streams, C * (S + T - 1)), dtype=torch.complex64, device="cuda", generator=g)
-    G = torch.randn((n_streams, S, C), dtype=torch.complex64, device="cuda", generator=g)
-    with ppf.Plan(C, T, synth.design_taps(C, T), "cf32", "c64") as plan:
+    sigma = {"ci8": 16.0, "ci16": 2000.0, "cf32": 1.0}[in_dtype]
+    xs = [synth.stream_torch(C, S + T - 1, in_dtype, sigma, synth.SEED_BASE + 21 + i, (), device="cuda")
+          for i in range(n_streams)]
+    x = xs[0] if n_streams == 1 else torch.stack(xs)
+    G = torch.randn((n_streams, S, C) if n_streams > 1 else (S, C), dtype=torch.complex64, device="cuda", generator=g)
+    with ppf.Plan(C, T, synth.design_taps(C, T), in_dtype, "c64") as plan:
         ms = _events(lambda: plan.backward(G, x), warmup, reps)
         plan.check_device()
-    b = n_streams * (C * S * 8 + 2 * C * (S + T - 1) * 8)
-    return {"case": "backward", "C": C, "T": T, "spectra": S, "streams": n_streams, "ms": ms,
+    b = n_streams * (C * S * 8 + C * (S + T - 1) * (synth.in_bytes_per_sample(in_dtype) + 8))
+    return {"case": "backward", "C": C, "T": T, "in": in_dtype, "spectra": S, "streams": n_streams, "ms": ms,
             "gsps": n_streams * C * S / ms / 1e6, "GB_s": b / ms / 1e6}
 
 
@@ -75,6 +78,7 @@ def main(argv=None):
     bw = sub.add_parser("backward")
     bw.add_argument("C", type=int)
     bw.add_argument("T", type=int)
+    bw.add_argument("in_dtype", nargs="?", default="cf32", choices=["ci8", "ci16", "cf32"])
     for p in (f, bw):
         p.add_argument("--spectra", type=int, default=None)
         p.add_argument("--streams", type=int, default=1)
@@ -85,7 +89,7 @@ def main(argv=None):
     if a.case == "forward":
         r = forward(a.C, a.T, a.in_dtype, a.out_dtype, S, a.streams, a.warmup, a.reps)
     else:
-        r = backward(a.C, a.T, S, a.streams, a.warmup, a.reps)
+        r = backward(a.C, a.T, a.in_dtype, S, a.streams, a.warmup, a.reps)
     print(json.dumps(r), flush=True)
 
 

@@ -70,13 +70,13 @@ def test_backward_single_outputs(mods):
 
 def test_backward_unsupported_shapes_raise(mods):
     ppf, _ = mods
-    with ppf.Plan(512, 8, synth.design_taps(512, 8), "cf32", "c64") as plan:
+    with ppf.Plan(1024, 8, synth.design_taps(1024, 8), "cf32", "c64") as plan:
         with pytest.raises(ppf.PPFError) as ei:
-            plan.backward(torch.zeros(4, 512, dtype=torch.complex64, device="cuda"),
-                          torch.zeros(11 * 512, dtype=torch.complex64, device="cuda"))
+            plan.backward(torch.zeros(4, 1024, dtype=torch.complex64, device="cuda"),
+                          torch.zeros(11 * 1024, dtype=torch.complex64, device="cuda"))
         assert ei.value.status == 2
     with ppf.Plan(256, 8, synth.design_taps(256, 8), "ci8", "c64") as plan:
-        with pytest.raises(TypeError):
+        with pytest.raises(TypeError):      # the input must have the plan's input type
             plan.backward(torch.zeros(4, 256, dtype=torch.complex64, device="cuda"),
                           torch.zeros(11 * 256, dtype=torch.complex64, device="cuda"))
 
@@ -208,3 +208,38 @@ def test_closed_form_leakage_gradient_matches_autograd(mods):
     loss, gY = fit.leakage_loss_and_grad(Y.detach(), fit._inband(k, C, Y.device))
     assert abs(float(loss) - float(ref)) <= 1e-6 * abs(float(ref))
     assert oracle.rel_l2(gY.cpu().numpy(), Y.grad.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("C,T,S,ns,in_dtype", [(512, 8, 300, 2, "cf32"), (512, 8, 1000, 1, "ci8"),
+                                               (512, 5, 77, 3, "ci16"), (256, 16, 500, 2, "ci8"),
+                                               (128, 4, 900, 1, "ci16"), (512, 1, 40, 1, "ci8")])
+def test_backward_wide_channels_and_integer_input(mods, C, T, S, ns, in_dtype):
+    """The adjoint at C = 512 (inverse DFT spread over the CTA) and with 8/16-bit input:
+    tap gradient against the oracle's (the input gradient is complex FP32 per input sample)."""
+    ppf, _ = mods
+    rng = np.random.default_rng(C + T + S)
+    sig = {"ci8": 16.0, "ci16": 2000.0, "cf32": 1.0}[in_dtype]
+    h = synth.design_taps(C, T) + 0.01 * rng.standard_normal(C * T).astype(np.float32)
+    xs = np.stack([synth.stream(C, S + T - 1, in_dtype, sig, 700 + i) for i in range(ns)])
+    G = crand(rng, ns, S, C)
+    with ppf.Plan(C, T, h, in_dtype, "c64") as plan:
+        xd = torch.from_numpy(xs if ns > 1 else xs[0]).cuda()
+        gx, gh = plan.backward(torch.from_numpy(G if ns > 1 else G[0]).cuda(), xd)
+        torch.cuda.synchronize()
+        plan.check_device()
+    gx = gx.cpu().numpy().astype(np.complex128).reshape(ns, -1)
+    gh = gh.cpu().numpy().astype(np.float64)
+    ref_gx = np.stack([oracle.pfb_grad_input(G[i].astype(np.complex128), h, C, T) for i in range(ns)])
+    ref_gh = sum(oracle.pfb_grad_taps(G[i].astype(np.complex128), xs[i], C, T) for i in range(ns))
+    assert oracle.rel_l2(gx, ref_gx) <= 1e-5
+    assert oracle.rel_l2(gh, ref_gh) <= 1e-4
+
+
+def test_backward_unsupported_shape_is_rejected(mods):
+    ppf, _ = mods
+    with ppf.Plan(512, 16, synth.design_taps(512, 16), "cf32", "c64") as plan:
+        G = torch.zeros((10, 512), dtype=torch.complex64, device="cuda")
+        x = torch.zeros(512 * 25, dtype=torch.complex64, device="cuda")
+        with pytest.raises(ppf.PPFError) as ei:
+            plan.backward(G, x)
+        assert ei.value.status == 2

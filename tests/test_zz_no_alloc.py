@@ -70,6 +70,32 @@ def test_noalloc_backward_matches_backward_twice(ppf):
             assert oracle.rel_l2(gh_n.cpu().numpy(), gh_r.cpu().numpy()) <= 1e-4
 
 
+def test_noalloc_grid_is_capped_by_the_fixed_array(ppf):
+    """At C=512, T=8 the fixed array holds 524,288 / (8 * 512) = 128 rows of partial
+    sums, fewer than the CTAs the plain call launches (one per SM): the capped grid
+    still gives the oracle's gradients, twice in a row, with different inputs."""
+    C, T, S = 512, 8, 2000
+    assert torch.cuda.get_device_properties(0).multi_processor_count > (1 << 19) // (T * C)
+    rng = np.random.default_rng(2026)
+    h = synth.design_taps(C, T)
+    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+        for seed in (1, 2):
+            x = synth.stream(C, S + T - 1, "ci8", 16.0, 900 + seed)
+            xd = torch.from_numpy(x).cuda()
+            G = torch.from_numpy((rng.standard_normal((S, C)) + 1j * rng.standard_normal((S, C))).astype(np.complex64)).cuda()
+            gx = torch.empty(C * (S + T - 1), dtype=torch.complex64, device="cuda")
+            gh = torch.empty(C * T, dtype=torch.float32, device="cuda")
+            st = ppf.lib().ppf_backward_noalloc(plan.handle, ctypes.c_void_p(G.data_ptr()), ctypes.c_void_p(xd.data_ptr()),
+                                                ctypes.c_void_p(gx.data_ptr()), ctypes.c_void_p(gh.data_ptr()), S, 1,
+                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+            ppf.check(st)
+            torch.cuda.synchronize()
+            plan.check_device()
+            Gn = G.cpu().numpy().astype(np.complex128)
+            assert oracle.rel_l2(gx.cpu().numpy(), oracle.pfb_grad_input(Gn, h, C, T)) <= 1e-5
+            assert oracle.rel_l2(gh.cpu().numpy(), oracle.pfb_grad_taps(Gn, x, C, T)) <= 1e-4
+
+
 def test_noalloc_many_streams_match_backward(ppf):
     """CTAs share the batches of all streams, so any stream count fits the fixed array."""
     rng = np.random.default_rng(2025)
