@@ -129,11 +129,17 @@ ppf_status ppf_execute_batched(ppf_plan_t plan, const void* in_dev, long long in
  *   grad_in_dev  : n_streams * C*(n_spectra+T-1) complex FP32, one per input
  *                  sample (written, not accumulated), or NULL
  *   grad_taps_dev: C*T floats (written), or NULL; not both NULL
- * Needs C in [64, 512] and T <= 16, and T <= 8 at C = 512 (else UNSUPPORTED).
- * The tap gradient is a deterministic two-pass reduction
- * (per-CTA partial sums, then a fixed-order sum); the partial-sum scratch is
- * allocated by the plan on the first call and grown when a call needs more
- * CTAs (cudaMalloc inside the call).  Asynchronous on `stream`.
+ * Every shape the plan accepts is supported.  For C in [64, 512] with
+ * T <= 16 (T <= 8 at C = 512) one fused kernel computes all three sums; for
+ * the other shapes (C = 32, C >= 1024, C = 3*2^k, T = 17..64, and T > 8 at
+ * C = 512) three passes run instead: the inverse DFT into a g_y scratch of
+ * n_streams*n_spectra*C complex FP32 owned by the plan, then grad_in, then
+ * the tap-gradient partial sums.  grad_in must not overlap grad_out or the
+ * input.  The tap gradient is a deterministic two-pass reduction (partial
+ * sums per CTA or per part of the rows, then a fixed-order sum).  The
+ * partial-sum and g_y scratch are allocated by the plan on the first call
+ * and grown when a call needs more (cudaMalloc inside the call).
+ * Asynchronous on `stream`.
  * If a bounded device wait gives up (ppf_check_device then reports
  * PPF_ERR_DEVICE_TIMEOUT), grad_in is incomplete and every element of
  * grad_taps is NaN; the plan's status word stays set until ppf_check_device
@@ -149,9 +155,11 @@ ppf_status ppf_backward(ppf_plan_t plan, const void* grad_out_dev, const void* i
  * fixed at start-up, or code where a cudaMalloc -- which may synchronise the
  * device or fail under memory pressure -- is not allowed).  The paper has no
  * counterpart; this is a deployment convenience.  Same arguments, results
- * and errors as ppf_backward, but the per-CTA tap-gradient partial sums live
- * in one fixed 2 MiB array (524,288 floats) inside the library instead of
- * plan memory, and the call allocates nothing.  The plan itself (made once
+ * and errors as ppf_backward for the shapes of its fused kernel (C in
+ * [64, 512], T <= 16, T <= 8 at C = 512; other shapes: UNSUPPORTED, since the
+ * three-pass path needs a g_y scratch), but the per-CTA tap-gradient partial
+ * sums live in one fixed 2 MiB array (524,288 floats) inside the library
+ * instead of plan memory, and the call allocates nothing.  The plan itself (made once
  * at set-up with ppf_plan) still owns the taps and tables.
  *   - Size limit: each CTA needs a row of tap_bucket*C floats; the call uses
  *     at most 524,288 / (tap_bucket*C) CTAs (128 at C=256, T=16 or C=512,
@@ -286,12 +294,18 @@ ppf_status ppf_plan_info(ppf_plan_t plan, int info[8]);
 ppf_status ppf_check_device(ppf_plan_t plan, ppf_stream_t stream);
 
 /*
- * ppf_set_debug_flags -- testing aid.  flags = 1 makes every later launch of
- * the plan's staged-input kernel wait on a barrier that nothing completes, so
- * the bounded wait runs out (after 2 ms) and the timeout path is exercised
- * without faulting the GPU; flags = 0 restores normal operation.
- * Errors: INVALID_ARG.
+ * ppf_set_debug_flags -- testing aids, a bitwise OR of:
+ *   PPF_DEBUG_INJECT_TIMEOUT (1): every later launch of the plan's
+ *     staged-input kernel waits on a barrier that nothing completes, so the
+ *     bounded wait runs out (after 2 ms) and the timeout path is exercised
+ *     without faulting the GPU;
+ *   PPF_DEBUG_UNFUSED_ADJOINT (2): ppf_backward runs its three-pass path even
+ *     where the fused adjoint kernel exists (to compare the two paths;
+ *     ppf_backward_noalloc ignores it).
+ * flags = 0 restores normal operation.  Errors: INVALID_ARG (unknown bit).
  */
+#define PPF_DEBUG_INJECT_TIMEOUT 1
+#define PPF_DEBUG_UNFUSED_ADJOINT 2
 ppf_status ppf_set_debug_flags(ppf_plan_t plan, int flags);
 
 /*

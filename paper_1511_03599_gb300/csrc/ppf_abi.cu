@@ -14,6 +14,7 @@
 
 #include "../../include/ppf.h"
 #include "ppf_bwd.cuh"
+#include "ppf_bwd_unfused.cuh"
 #include "ppf_fwd.cuh"
 #include "ppf_internal.h"
 
@@ -94,6 +95,16 @@ bool lookup_fir(int C, int tm, int in, ppf::FwdEntry* e) {
     }
 }
 
+bool lookup_idft(int C, ppf::IdftEntry* e) {
+    switch (C) {
+#define PPF_ID(CC) case CC: return ppf::idft_lookup_c##CC(e);
+        PPF_ID(32) PPF_ID(64) PPF_ID(128) PPF_ID(256) PPF_ID(512) PPF_ID(1024) PPF_ID(2048) PPF_ID(4096)
+        PPF_ID(384) PPF_ID(768) PPF_ID(1536) PPF_ID(3072)
+#undef PPF_ID
+        default: return false;
+    }
+}
+
 bool twiddles(int C, std::vector<float>& pairs) {
     int n = 0;
     switch (C) {
@@ -134,8 +145,12 @@ struct ppf_plan_s {
     bool has_bwd;         // adjoint kernel available for this shape
     ppf::BwdEntry bwd;
     int bwd_occupancy;
-    float* d_partials;    // tap-gradient partial sums, one row of TM*C per CTA
+    float* d_partials;    // tap-gradient partial sums, one row of TM*C per CTA (or per part)
     long long partials_ctas;
+    ppf::IdftEntry idft;  // unfused adjoint: inverse DFT pass
+    int idft_occupancy;
+    float2* d_gy;         // unfused adjoint: g_y scratch
+    size_t gy_bytes;
     bool has_fir;         // FIR-only ablation kernel available for this shape
     ppf::FwdEntry fir;
     int fir_grid;
@@ -243,6 +258,16 @@ extern "C" ppf_status ppf_plan(ppf_plan_t* out, int C, int T, const float* coeff
             return cuda_fail(ce, "ppf_plan: backward kernel attributes");
         }
         p->has_bwd = p->bwd_occupancy > 0;
+    }
+    if (lookup_idft(C, &p->idft)) {
+        ce = cudaFuncSetAttribute(p->idft.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->idft.smem);
+        if (ce == cudaSuccess)
+            ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p->idft_occupancy, p->idft.fn, p->idft.threads,
+                                                               p->idft.smem);
+        if (ce != cudaSuccess) {
+            delete p;
+            return cuda_fail(ce, "ppf_plan: inverse-DFT kernel attributes");
+        }
     }
     if (lookup_fir(C, tm, (int)in_dtype, &p->fir)) {
         int focc = 0;
@@ -358,12 +383,89 @@ extern "C" ppf_status ppf_execute(ppf_plan_t p, const void* in_dev, void* out_de
     return ppf_execute_batched(p, in_dev, 0, out_dev, 0, n_spectra, 1, stream);
 }
 
+// The unfused adjoint: inverse DFT of G into the plan's g_y scratch, then
+// the grad_x pass and the grad_h partial sums + fixed-order reduction.
+static ppf_status backward_unfused(ppf_plan_t p, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
+                                   float* grad_taps_dev, long long n_spectra, long long n_streams, cudaStream_t st) {
+    const int C = p->C, T = p->T, TM = p->TM;
+    if (p->idft.fn == nullptr || p->idft_occupancy < 1)
+        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward: no inverse-DFT kernel for C=%d", C);
+    const long long n_raw = n_spectra + T - 1;
+    const size_t gy_bytes = (size_t)n_streams * n_spectra * C * 8;
+    cudaError_t ce;
+    if (gy_bytes > p->gy_bytes) {   // g_y scratch, grown when a call needs more
+        if (p->d_gy) cudaFree(p->d_gy);
+        p->d_gy = nullptr;
+        p->gy_bytes = 0;
+        ce = cudaMalloc(&p->d_gy, gy_bytes);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: g_y scratch");
+        p->gy_bytes = gy_bytes;
+    }
+    ppf::IdftArgs ia;
+    ia.gY = static_cast<const float2*>(grad_out_dev);
+    ia.gy = p->d_gy;
+    ia.tw = p->d_tw;
+    ia.n_spectra = n_spectra;
+    ia.gY_stride = n_spectra * C;
+    ia.n_streams = n_streams;
+    const long long idft_grid = work_units((long long)p->sms * p->idft_occupancy, n_streams,
+                                           (n_spectra + p->idft.batch - 1) / p->idft.batch);
+    ce = p->idft.launch(ia, (int)idft_grid, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: inverse DFT launch");
+    if (grad_in_dev != nullptr) {
+        ppf::AdjFirArgs fa;
+        fa.gy = p->d_gy;
+        fa.taps = p->d_taps;
+        fa.gx = static_cast<float2*>(grad_in_dev);
+        fa.n_spectra = n_spectra;
+        fa.n_streams = n_streams;
+        fa.gx_stride = n_raw * C;
+        fa.C = C;
+        fa.T = T;
+        const long long tiles = n_streams * ((n_raw + ppf::kAdjL - 1) / ppf::kAdjL);
+        const long long pair_blocks = (C / 2 + 127) / 128;
+        const long long gx_grid = std::min<long long>(tiles, std::max<long long>(1, 16LL * p->sms / pair_blocks));
+        ce = ppf::bwd_gradx(fa, (int)gx_grid, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: grad_in launch");
+    }
+    if (grad_taps_dev != nullptr) {
+        // parts of the rows of all streams: about 8 CTAs per SM in all, at
+        // least 64 rows per part, partial sums capped at 2^25 floats
+        const long long blocks = ((C / 2 + 127) / 128) * (long long)ppf::bwd_gradh_tap_blocks(T);
+        long long parts = std::max<long long>(1, (8LL * p->sms + blocks - 1) / blocks);
+        parts = std::min<long long>(parts, std::max<long long>(1, n_streams * n_spectra / 64));
+        parts = std::min<long long>(parts, std::max<long long>(1, (1LL << 25) / ((long long)TM * C)));
+        if (parts > p->partials_ctas) {
+            if (p->d_partials) cudaFree(p->d_partials);
+            p->d_partials = nullptr;
+            p->partials_ctas = 0;
+            ce = cudaMalloc(&p->d_partials, sizeof(float) * (size_t)parts * TM * C);
+            if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: partial sums");
+            p->partials_ctas = parts;
+        }
+        ppf::AdjCorrArgs ca;
+        ca.gy = p->d_gy;
+        ca.x = in_dev;
+        ca.partials = p->d_partials;
+        ca.n_spectra = n_spectra;
+        ca.n_streams = n_streams;
+        ca.x_stride = n_raw * C;
+        ca.C = C;
+        ca.T = T;
+        ca.TM = TM;
+        ca.n_parts = (int)parts;
+        ce = ppf::bwd_gradh((int)p->in, ca, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: grad_taps launch");
+        ce = ppf::bwd_reduce(p->d_partials, (int)parts, T, TM, C, p->d_err, grad_taps_dev, st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "ppf_backward: tap-gradient reduction");
+    }
+    return PPF_OK;
+}
+
 extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const void* in_dev, void* grad_in_dev,
                                    float* grad_taps_dev, long long n_spectra, long long n_streams,
                                    ppf_stream_t stream) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: invalid plan");
-    if (!p->has_bwd)
-        return fail(PPF_ERR_UNSUPPORTED, "ppf_backward: needs C in [64, 512] with T <= 16 (T <= 8 at C = 512)");
     if (grad_out_dev == nullptr || in_dev == nullptr || (grad_in_dev == nullptr && grad_taps_dev == nullptr))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: NULL buffer");
     if (n_spectra < 1 || n_streams < 1) return fail(PPF_ERR_INVALID_ARG, "ppf_backward: empty problem");
@@ -377,6 +479,11 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
     if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), in_dev,
                                 (unsigned long long)(n_streams * in_len * bytes_in(p->in))))
         return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps the input");
+    if (grad_in_dev && overlaps(grad_in_dev, (unsigned long long)(n_streams * in_len * 8), grad_out_dev,
+                                (unsigned long long)(n_streams * out_len * 8)))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_backward: grad_in overlaps grad_out");
+    if (!p->has_bwd || (p->debug_flags & PPF_DEBUG_UNFUSED_ADJOINT))
+        return backward_unfused(p, grad_out_dev, in_dev, grad_in_dev, grad_taps_dev, n_spectra, n_streams, st);
     const long long nb = (n_raw + p->bwd.batch - 1) / p->bwd.batch;
     // one wave of resident CTAs sharing the batches of all streams equally
     const long long grid = work_units((long long)p->sms * p->bwd_occupancy, n_streams, nb);
@@ -486,6 +593,7 @@ extern "C" ppf_status ppf_destroy(ppf_plan_t p) {
     if (p->d_tw) cudaFree(p->d_tw);
     if (p->d_err) cudaFree(p->d_err);
     if (p->d_partials) cudaFree(p->d_partials);
+    if (p->d_gy) cudaFree(p->d_gy);
     p->magic = 0;
     delete p;
     return PPF_OK;
@@ -522,7 +630,8 @@ extern "C" ppf_status ppf_check_device(ppf_plan_t p, ppf_stream_t stream) {
 
 extern "C" ppf_status ppf_set_debug_flags(ppf_plan_t p, int flags) {
     if (!valid_plan(p)) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: invalid plan");
-    if (flags & ~ppf::FWD_INJECT_TIMEOUT) return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: unknown flag");
+    if (flags & ~(PPF_DEBUG_INJECT_TIMEOUT | PPF_DEBUG_UNFUSED_ADJOINT))
+        return fail(PPF_ERR_INVALID_ARG, "ppf_set_debug_flags: unknown flag");
     p->debug_flags = flags;
     return PPF_OK;
 }

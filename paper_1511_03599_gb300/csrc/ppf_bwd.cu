@@ -1,7 +1,9 @@
-// ppf_bwd.cu -- instantiates the PFB adjoint kernels (complex int8 / int16 /
-// FP32 input, C in {64, 128, 256, 512}, tap buckets up to 16 where the batch
-// holds the halo) and exports their lookup.
+// ppf_bwd.cu -- instantiates the fused PFB adjoint kernels (complex int8 /
+// int16 / FP32 input, C in {64, 128, 256, 512}, tap buckets up to 16 where
+// the batch holds the halo) and the runtime-shape passes of the unfused
+// adjoint, and exports their lookups and launches.
 #include "ppf_bwd.cuh"
+#include "ppf_bwd_unfused.cuh"
 #include "ppf_internal.h"
 
 namespace ppf {
@@ -50,6 +52,26 @@ cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, 
                        cudaStream_t st) {
     const int TC = T * C;
     pfb_bwd_reduce_kernel<<<(TC + 255) / 256, 256, 0, st>>>(partials, nparts, TC, TM * C, err, grad_h);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t bwd_gradx(const AdjFirArgs& a, int grid_x, cudaStream_t st) {
+    const int pairs = a.C / 2, nt = pairs < 128 ? pairs : 128;
+    pfb_bwd_gradx_kernel<<<dim3(grid_x, (pairs + nt - 1) / nt), nt, 0, st>>>(a);
+    return cudaPeekAtLastError();
+}
+
+int bwd_gradh_tap_blocks(int T) { return (T + kAdjTB - 1) / kAdjTB; }
+
+cudaError_t bwd_gradh(int in, const AdjCorrArgs& a, cudaStream_t st) {
+    const int pairs = a.C / 2, nt = pairs < 128 ? pairs : 128;
+    const dim3 grid(a.n_parts, (pairs + nt - 1) / nt, bwd_gradh_tap_blocks(a.T));
+    switch (in) {
+        case IN_CI8: pfb_bwd_gradh_kernel<IN_CI8><<<grid, nt, 0, st>>>(a); break;
+        case IN_CI16: pfb_bwd_gradh_kernel<IN_CI16><<<grid, nt, 0, st>>>(a); break;
+        case IN_CF32: pfb_bwd_gradh_kernel<IN_CF32><<<grid, nt, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaPeekAtLastError();
 }
 

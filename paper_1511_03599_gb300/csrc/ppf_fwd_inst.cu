@@ -1,6 +1,8 @@
 // ppf_fwd_inst.cu -- instantiates the fused forward kernel for one channel
 // count C (compiled once per C with -DPPF_C=<C>) over every tap bucket,
-// input type and output type, and exports the lookup used by the C ABI.
+// input type and output type, and the inverse DFT of the unfused adjoint,
+// and exports the lookups used by the C ABI.
+#include "ppf_bwd_unfused.cuh"
 #include "ppf_fwd.cuh"
 #include "ppf_internal.h"
 
@@ -79,6 +81,12 @@ bool PPF_CAT(fir_lookup_c, PPF_C)(int tm, int in, FwdEntry* e) {
         case 16: return fir_by_in<16>(in, e);
         default: return false;
     }
+}
+
+bool PPF_CAT(idft_lookup_c, PPF_C)(IdftEntry* e) {
+    const IdftInfo i = idft_info<PPF_C>();
+    *e = IdftEntry{i.threads, i.batch, i.smem, i.fn, &idft_launch<PPF_C>};
+    return true;
 }
 
 int PPF_CAT(fwd_twiddle_count_c, PPF_C)() { return tw_total_float2s(PPF_C) > 0 ? tw_total_float2s(PPF_C) : 1; }

@@ -15,6 +15,9 @@ ppf_status set_error(ppf_status s, const char* fmt, ...);
 
 struct FwdArgs;
 struct BwdArgs;
+struct IdftArgs;
+struct AdjFirArgs;
+struct AdjCorrArgs;
 
 struct FwdEntry {
     int threads;     // threads per CTA
@@ -45,10 +48,27 @@ bool bwd_lookup(int C, int tap_bucket, int in, BwdEntry* e);
 cudaError_t bwd_reduce(const float* partials, int nparts, int T, int TM, int C, const int* err, float* grad_h,
                        cudaStream_t st);
 
+// Unfused adjoint (any planned shape): inverse DFT per C, then the
+// transposed FIR and the tap correlation (runtime C and T).
+struct IdftEntry {
+    int threads;     // threads per CTA
+    int batch;       // spectra per CTA batch
+    int smem;        // dynamic shared memory bytes
+    const void* fn;
+    cudaError_t (*launch)(const IdftArgs&, int grid, cudaStream_t);
+};
+// grad_x pass; grid_x: CTAs along the row tiles of all streams.
+cudaError_t bwd_gradx(const AdjFirArgs& a, int grid_x, cudaStream_t st);
+// grad_h partial sums (a.n_parts parts of the rows of all streams).
+cudaError_t bwd_gradh(int in, const AdjCorrArgs& a, cudaStream_t st);
+// Tap blocks of the grad_h pass (partial-sum rows are TM*C floats).
+int bwd_gradh_tap_blocks(int T);
+
 // Per-C lookups; return false when the (tap bucket, in, out) triple is not built.
 #define PPF_DECLARE_C(C)                                                         \
     bool fwd_lookup_c##C(int tap_bucket, int in, int out, FwdEntry* e);         \
     bool fir_lookup_c##C(int tap_bucket, int in, FwdEntry* e);                  \
+    bool idft_lookup_c##C(IdftEntry* e);                                         \
     int fwd_twiddle_count_c##C();                                                \
     void fwd_twiddles_c##C(float* host_pairs);
 PPF_DECLARE_C(32)

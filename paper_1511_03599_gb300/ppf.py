@@ -266,7 +266,8 @@ class Plan:
         check(lib().ppf_check_device(self.handle, _stream_handle(stream)))
 
     def set_debug_flags(self, flags: int):
-        """Testing aid: 1 makes launches run out a bounded wait (see ppf.h)."""
+        """Testing aids (see ppf.h): 1 makes launches run out a bounded wait,
+        2 makes backward() take its three-pass path where the fused kernel exists."""
         check(lib().ppf_set_debug_flags(self.handle, int(flags)))
 
     def close(self):

@@ -115,3 +115,24 @@ def test_noalloc_many_streams_match_backward(ppf):
         assert oracle.rel_l2(gh_n.cpu().numpy(), ref_gh) <= 1e-4
         assert oracle.rel_l2(gx_n.cpu().numpy(), gx_r.cpu().numpy()) <= 1e-5
         assert oracle.rel_l2(gh_n.cpu().numpy(), gh_r.cpu().numpy()) <= 1e-4
+
+
+def test_noalloc_rejects_shapes_outside_the_fused_kernel(ppf):
+    """C = 512 with T = 16 needs ppf_backward's three-pass path (a g_y scratch):
+    ppf_backward runs it, ppf_backward_noalloc returns UNSUPPORTED and
+    allocates nothing."""
+    C, T, S, ns = 512, 16, 20, 1
+    rng = np.random.default_rng(5)
+    h = synth.design_taps(C, T)
+    with ppf.Plan(C, T, h, "cf32", "c64") as plan:
+        x = torch.from_numpy((rng.standard_normal((ns, C * (S + T - 1)))
+                              + 1j * rng.standard_normal((ns, C * (S + T - 1)))).astype(np.complex64)).cuda()
+        G = torch.from_numpy((rng.standard_normal((ns, S, C))
+                              + 1j * rng.standard_normal((ns, S, C))).astype(np.complex64)).cuda()
+        gx_r, gh_r = _call(ppf, "ppf_backward", plan, G, x, S, ns)
+        ref_gx, ref_gh = _oracle_grads(G, x, h, C, T)
+        assert oracle.rel_l2(gx_r.cpu().numpy(), ref_gx) <= 1e-5
+        assert oracle.rel_l2(gh_r.cpu().numpy(), ref_gh) <= 1e-4
+        with pytest.raises(ppf.PPFError) as ei:
+            _call(ppf, "ppf_backward_noalloc", plan, G, x, S, ns)
+        assert ei.value.status == 2
