@@ -132,12 +132,14 @@ __device__ __forceinline__ float2 cmul_tw(float2 a) {
         return make_float2(-a.x, -a.y);
     } else if constexpr (4 * m == 3 * N) {             // +i
         return make_float2(-a.y, a.x);
-    } else if constexpr (8 * m == N) {                 // (1 - i)/sqrt2
+    } else if constexpr (8 * m == N) {                 // (1 - i)/sqrt2: (x + y) r, (y - x) r
         constexpr float r = Tw<1, 8>::re;
-        return make_float2((a.x + a.y) * r, (a.y - a.x) * r);
-    } else if constexpr (8 * m == 3 * N) {             // (-1 - i)/sqrt2
+        const float t = a.y * r;                      // 3 instructions: y r, then x r +/- y r fused
+        return make_float2(fmaf(a.x, r, t), fmaf(-a.x, r, t));
+    } else if constexpr (8 * m == 3 * N) {             // (-1 - i)/sqrt2: (y - x) r, -(x + y) r
         constexpr float r = Tw<1, 8>::re;
-        return make_float2((a.y - a.x) * r, -(a.x + a.y) * r);
+        const float t = a.y * r;
+        return make_float2(fmaf(-a.x, r, t), fmaf(-a.x, r, -t));
     } else {
         constexpr float wr = Tw<m, N>::re, wi = Tw<m, N>::im;
         return make_float2(fmaf(a.x, wr, -a.y * wi), fmaf(a.x, wi, a.y * wr));
@@ -338,6 +340,17 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
         "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_addr(dst_smem)),
         "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// The same copy with an L2 evict-first policy for the source lines (data
+// read exactly once, so it need not displace the output lines in L2).
+__device__ __forceinline__ void tma_load_1d_once(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
         : "memory");
 }
 // Hint: bring a global range into L2 ahead of its use (bytes multiple of 16).

@@ -24,6 +24,12 @@
 
 #include "ppf_fwd.cuh"
 
+// Raw batches are copied with an L2 evict-first policy (each is read once):
+// +0.1-0.3 % on every measured shape, the output's lines stay in L2 longer.
+#ifndef PPF_TMA_EVICT_FIRST
+#define PPF_TMA_EVICT_FIRST 1
+#endif
+
 namespace ppf {
 
 // every FFT stage must give each thread a whole number (>= 1) of items
@@ -143,6 +149,39 @@ pfb_fwd_carry_kernel(FwdArgs args) {
     const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
     const long long nraw_b = (T > 1) ? nb + 1 : nb;  // raw batches this CTA streams
 
+    auto rows_of = [&](long long j) -> long long {
+        const long long r = n_raw - (lo + j) * B;
+        return r <= 0 ? 0 : (r < B ? r : B);
+    };
+    auto issue = [&](long long j) {
+        const long long rows = rows_of(j);
+        if (rows > 0) {
+            uint64_t* bar = &bars[j & 1];
+            const uint32_t bytes = (uint32_t)(rows * C * BIN);
+            mbar_expect_tx(bar, bytes);
+            if constexpr (PPF_TMA_EVICT_FIRST)
+                tma_load_1d_once(ring + (j & 1) * S::SLOTB,
+                                 static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
+            else
+                tma_load_1d(ring + (j & 1) * S::SLOTB,
+                            static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
+        }
+    };
+    // fp32 input: the first two raw batches are requested before the taps,
+    // the carried rows and the twiddles are loaded, so their latencies
+    // overlap (+1 % at C = 512; for 8/16-bit input it measured 0.1-0.2 %
+    // slower, so there they are requested after the CTA barrier below)
+    constexpr bool EARLY = IN == IN_CF32;
+    if (tid == 0) {
+        for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
+        fence_mbar_init();
+        *sflag = 0;
+        if (EARLY) {
+            issue(0);
+            if (nraw_b > 1) issue(1);
+        }
+    }
+
     const float2* tws = args.tw;
     if constexpr (S::TW_SMEM) {
         for (int i = tid; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
@@ -168,27 +207,8 @@ pfb_fwd_carry_kernel(FwdArgs args) {
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    auto rows_of = [&](long long j) -> long long {
-        const long long r = n_raw - (lo + j) * B;
-        return r <= 0 ? 0 : (r < B ? r : B);
-    };
-    auto issue = [&](long long j) {
-        const long long rows = rows_of(j);
-        if (rows > 0) {
-            uint64_t* bar = &bars[j & 1];
-            const uint32_t bytes = (uint32_t)(rows * C * BIN);
-            mbar_expect_tx(bar, bytes);
-            tma_load_1d(ring + (j & 1) * S::SLOTB,
-                        static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * BIN, bytes, bar);
-        }
-    };
-    if (tid == 0) {
-        for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
-        fence_mbar_init();
-        *sflag = 0;
-    }
     __syncthreads();
-    if (tid == 0) {
+    if (!EARLY && tid == 0) {
         issue(0);
         if (nraw_b > 1) issue(1);
     }
