@@ -313,6 +313,31 @@ def measure_fwd_bwd_headline(plan, w, x, y, steps: int, warmup: int, dev):
             "bwd_bytes_per_sample": 8 + b_in + 8}
 
 
+def measure_fwd_bwd_shape(C: int, T: int, in_dtype: str, S: int, steps: int, warmup: int, dev):
+    """Forward vs forward + adjoint (both gradients) for one single-stream
+    shape; outside the fused adjoint kernel's shapes the adjoint is the
+    three-pass path (inverse DFT, transposed FIR, tap correlation)."""
+    import torch
+    from paper_1511_03599_gb300 import ppf, synth
+    st = torch.cuda.current_stream()
+    sigma = {"ci8": 16.0, "ci16": 2000.0, "cf32": 1.0}[in_dtype]
+    x = synth.stream_torch(C, S + T - 1, in_dtype, sigma, synth.SEED_BASE + 7, (), device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_BASE + 8)
+    G = torch.randn((S, C), dtype=torch.complex64, device=dev, generator=g)
+    with ppf.Plan(C, T, synth.design_taps(C, T), in_dtype, "c64") as plan:
+        y = plan.empty_output(S, device=dev)
+        t_f = time_launches(lambda: plan.execute(x, out=y, stream=st), steps, warmup, st)
+        t_fb = time_launches(lambda: (plan.execute(x, out=y, stream=st), plan.backward(G, x, stream=st)),
+                             steps, warmup, st)
+        plan.check_device()
+        fused = plan.info()  # launch shape of the forward
+    del x, G, y
+    return {"workload": f"pfb_c{C}_t{T}_s{S}_{in_dtype}_c64", "fwd_ms": t_f, "fwd_bwd_ms": t_fb,
+            "fwd_bwd_over_fwd": t_fb / t_f, "bwd_ms": t_fb - t_f, "fwd_launch": fused,
+            "backward": "three-pass: inverse DFT, transposed FIR, tap correlation + fixed-order reduction"}
+
+
 def measure_ablation(plan, x, y, steps: int, warmup: int, dev):
     """Fused kernel vs the unfused pair (FIR kernel, filtered spectra to HBM,
     then the DFT kernel) on the benchmark workload (E3 of the paper: the FIR/DFT
@@ -635,7 +660,7 @@ def main():
         e2e = {"value": world * samples / te / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
-               "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, 2-stream chunk pipeline"}
+               "ms_per_step": te * 1e3, "path": "ppf_execute_host, pinned host buffers, chunk pipeline on copy-in / compute / copy-out streams"}
         # the host link alone: the same bytes copied concurrently (D2H of the
         # output, H2D of the input) with no kernel -- the bound of this number
         try:
@@ -678,6 +703,10 @@ def main():
             fb["headline"] = measure_fwd_bwd_headline(plan, w, x, y, max(5, args.steps // 2), args.warmup, dev)
         except Exception as e:  # noqa: BLE001 - reported beside the metric
             fb["headline"] = {"error": str(e)}
+        try:
+            fb["long_taps"] = measure_fwd_bwd_shape(512, 32, "ci8", 1 << 18, max(5, args.steps // 2), args.warmup, dev)
+        except Exception as e:  # noqa: BLE001 - reported beside the metric
+            fb["long_taps"] = {"error": str(e)}
         try:
             from paper_1511_03599_gb300 import fit
             r = fit.fit_taps()

@@ -248,11 +248,12 @@ ppf_status ppf_fft(ppf_plan_t plan, const void* y_dev, void* out_dev, long long 
 
 /*
  * ppf_execute_host -- the same transform with HOST input and output buffers.
- * The stream is cut into chunks that are copied host->device, transformed
- * and copied device->host on a small pipeline of CUDA streams so that the
- * copies of chunk i+1 and i-1 overlap the compute of chunk i (the copy /
- * compute overlap of Sec. 5).  Device staging buffers are allocated on the
- * first call and kept by the plan.  Pinned host buffers give full copy speed;
+ * The stream is cut into chunks (about 64 MiB of output each) that are
+ * copied host->device, transformed and copied device->host on three CUDA
+ * streams, one per engine, so that the copies of chunk i+1 and i-1 overlap
+ * the compute of chunk i (the copy / compute overlap of Sec. 5) with at most
+ * one copy per direction in flight.  Three device staging slots per
+ * direction are allocated on the first call and kept by the plan.  Pinned host buffers give full copy speed;
  * pageable ones work but are slower.  Synchronous: returns when `out_host`
  * holds the result.  `stream` orders the call after earlier work on it.
  * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY.

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <new>
 #include <unordered_set>
@@ -122,12 +123,20 @@ int bytes_out(ppf_out_t t) { return t == PPF_OUT_CF32 ? 8 : 4; }
 }  // namespace
 
 // Host pipeline state of ppf_execute_host (allocated on first use).
+// Three streams, one per engine: host->device copies, kernels,
+// device->host copies, so at most one copy per direction is in flight (two
+// concurrent copies in one direction share the host link no faster) and
+// each engine works through its chunks in order.  kDepth staging slots;
+// events order a slot's reuse after its last reader.
 struct HostPipe {
-    static constexpr int kDepth = 2;
+    static constexpr int kDepth = 3;
     long long chunk = 0;                 // output spectra per chunk
-    cudaStream_t st[kDepth] = {nullptr, nullptr};
-    void* d_in[kDepth] = {nullptr, nullptr};
-    void* d_out[kDepth] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_cmp = nullptr, s_out = nullptr;
+    void* d_in[kDepth] = {};
+    void* d_out[kDepth] = {};
+    cudaEvent_t ev_in[kDepth] = {};      // slot's input landed
+    cudaEvent_t ev_cmp[kDepth] = {};     // slot's kernel done (input free, output ready)
+    cudaEvent_t ev_out[kDepth] = {};     // slot's output copied out (output free)
     cudaEvent_t start = nullptr;
 };
 
@@ -520,10 +529,13 @@ extern "C" ppf_status ppf_backward(ppf_plan_t p, const void* grad_out_dev, const
 
 static void free_pipe(HostPipe* hp) {
     if (hp == nullptr) return;
+    for (cudaStream_t st : {hp->s_in, hp->s_cmp, hp->s_out})
+        if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     for (int i = 0; i < HostPipe::kDepth; ++i) {
-        if (hp->st[i]) { cudaStreamSynchronize(hp->st[i]); cudaStreamDestroy(hp->st[i]); }
         if (hp->d_in[i]) cudaFree(hp->d_in[i]);
         if (hp->d_out[i]) cudaFree(hp->d_out[i]);
+        for (cudaEvent_t ev : {hp->ev_in[i], hp->ev_cmp[i], hp->ev_out[i]})
+            if (ev) cudaEventDestroy(ev);
     }
     if (hp->start) cudaEventDestroy(hp->start);
     delete hp;
@@ -544,11 +556,15 @@ extern "C" ppf_status ppf_execute_host(ppf_plan_t p, const void* in_host, void* 
         ch = ch / p->fwd.batch * p->fwd.batch;
         if (ch < p->fwd.batch) ch = p->fwd.batch;
         hp->chunk = ch;
-        ce = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
+        const unsigned evf = cudaEventDisableTiming;
+        ce = cudaEventCreateWithFlags(&hp->start, evf);
+        for (cudaStream_t* st : {&hp->s_in, &hp->s_cmp, &hp->s_out})
+            if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
         for (int i = 0; i < HostPipe::kDepth && ce == cudaSuccess; ++i) {
-            ce = cudaStreamCreateWithFlags(&hp->st[i], cudaStreamNonBlocking);
-            if (ce == cudaSuccess) ce = cudaMalloc(&hp->d_in[i], (size_t)C * (ch + T - 1) * bi);
+            ce = cudaMalloc(&hp->d_in[i], (size_t)C * (ch + T - 1) * bi);
             if (ce == cudaSuccess) ce = cudaMalloc(&hp->d_out[i], (size_t)C * ch * bo);
+            for (cudaEvent_t* ev : {&hp->ev_in[i], &hp->ev_cmp[i], &hp->ev_out[i]})
+                if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(ev, evf);
         }
         if (ce != cudaSuccess) {
             free_pipe(hp);
@@ -559,25 +575,39 @@ extern "C" ppf_status ppf_execute_host(ppf_plan_t p, const void* in_host, void* 
     HostPipe* hp = p->pipe;
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     ce = cudaEventRecord(hp->start, user);
-    for (int i = 0; i < HostPipe::kDepth && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(hp->st[i], hp->start, 0);
+    for (cudaStream_t st : {hp->s_in, hp->s_cmp, hp->s_out})
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, hp->start, 0);
     if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: stream ordering");
-    // chunk k on stream k % depth: H2D(k) -> kernel(k) -> D2H(k); the other
-    // stream's copies overlap this stream's kernel.
+    // chunk k in slot q = k % depth: H2D(k) on s_in after the kernel of chunk
+    // k-depth has read slot q; the kernel on s_cmp after H2D(k) and after the
+    // D2H of chunk k-depth has emptied output slot q; D2H(k) on s_out after
+    // the kernel.  (Each wait binds to the event's latest record, i.e. the
+    // one of chunk k-depth, or to none on the first use of a slot.)
     long long k = 0;
     for (long long s0 = 0; s0 < n_spectra; s0 += hp->chunk, ++k) {
         const int q = (int)(k % HostPipe::kDepth);
+        const bool reuse = k >= HostPipe::kDepth;
         const long long n = (n_spectra - s0 < hp->chunk) ? n_spectra - s0 : hp->chunk;
         const char* src = static_cast<const char*>(in_host) + (size_t)s0 * C * bi;
         char* dst = static_cast<char*>(out_host) + (size_t)s0 * C * bo;
-        ce = cudaMemcpyAsync(hp->d_in[q], src, (size_t)C * (n + T - 1) * bi, cudaMemcpyHostToDevice, hp->st[q]);
+        if (reuse) ce = cudaStreamWaitEvent(hp->s_in, hp->ev_cmp[q], 0);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(hp->d_in[q], src, (size_t)C * (n + T - 1) * bi, cudaMemcpyHostToDevice, hp->s_in);
+        if (ce == cudaSuccess) ce = cudaEventRecord(hp->ev_in[q], hp->s_in);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(hp->s_cmp, hp->ev_in[q], 0);
+        if (ce == cudaSuccess && reuse) ce = cudaStreamWaitEvent(hp->s_cmp, hp->ev_out[q], 0);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: host->device copy");
-        ppf_status s = launch_fwd(p, hp->d_in[q], 0, hp->d_out[q], 0, n, 1, hp->st[q]);
+        ppf_status s = launch_fwd(p, hp->d_in[q], 0, hp->d_out[q], 0, n, 1, hp->s_cmp);
         if (s != PPF_OK) return s;
-        ce = cudaMemcpyAsync(dst, hp->d_out[q], (size_t)C * n * bo, cudaMemcpyDeviceToHost, hp->st[q]);
+        ce = cudaEventRecord(hp->ev_cmp[q], hp->s_cmp);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(hp->s_out, hp->ev_cmp[q], 0);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(dst, hp->d_out[q], (size_t)C * n * bo, cudaMemcpyDeviceToHost, hp->s_out);
+        if (ce == cudaSuccess) ce = cudaEventRecord(hp->ev_out[q], hp->s_out);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: device->host copy");
     }
-    for (int i = 0; i < HostPipe::kDepth; ++i) {
-        ce = cudaStreamSynchronize(hp->st[i]);
+    for (cudaStream_t st : {hp->s_in, hp->s_cmp, hp->s_out}) {
+        ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) return cuda_fail(ce, "ppf_execute_host: synchronise");
     }
     return PPF_OK;
