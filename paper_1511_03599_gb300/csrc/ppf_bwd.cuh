@@ -33,7 +33,13 @@ namespace ppf {
 template <int C, int TM, int IN = IN_CF32>
 struct BwdShape {
     static constexpr int NT = C;                                     // one channel per thread
-    static constexpr int B = 4096 / C;                               // raw rows per batch
+    // C = 512 with 8/16-bit input and up to 8 taps: batches of 16 rows, so each
+    // of the 16 warps owns a whole spectrum in the inverse DFT (no CTA
+    // barriers between its stages); the per-channel sums run in two passes
+    // of 8 rows to keep the carried state in registers
+    static constexpr bool WIDE = C == 512 && IN != IN_CF32 && TM <= 8;
+    static constexpr int B = WIDE ? 16 : 4096 / C;                   // raw rows per batch
+    static constexpr int BF = WIDE ? 8 : B;                          // rows per pass of the channel sums
     static constexpr int BIN = InTraits<IN>::bytes;
     static constexpr int SLOTB = B * C * 8;                          // complex FP32 rows of G of a batch
     static constexpr int XSLOTB = B * C * BIN;                       // raw rows of x of a batch
@@ -43,8 +49,9 @@ struct BwdShape {
     static constexpr int SPW = NWARP > 0 && B >= NWARP ? B / NWARP : 0;
     static constexpr int TWB = tw_size(C) * 8;                       // twiddle tables
     static constexpr int SMEM = 2 * SLOTB + 2 * XSLOTB + TWB + 64;   // G slots, x slots, twiddles, barriers
-    static constexpr bool FFT_OK = SPW > 0 ? (SPW * NWARP == B && fft_items_fit(C, SPW, 32)) : C == 512;
-    static constexpr bool OK = (C >= 64 && C <= 512) && (TM <= 16) && (B >= TM - 1) && FFT_OK;
+    static constexpr bool FFT_OK = SPW > 0 ? (SPW * NWARP == B && (WIDE ? warp_fft_ok(C, SPW) : fft_items_fit(C, SPW, 32)))
+                                           : C == 512;
+    static constexpr bool OK = (C >= 64 && C <= 512) && (TM <= 16) && (BF >= TM - 1) && B % BF == 0 && FFT_OK;
 };
 
 struct BwdArgs {
@@ -65,7 +72,7 @@ struct BwdArgs {
 template <int C, int TM, int IN>
 __global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(BwdArgs args) {
     using S = BwdShape<C, TM, IN>;
-    constexpr int NT = S::NT, B = S::B, NST = fft_stages(C), BIN = S::BIN;
+    constexpr int NT = S::NT, B = S::B, BF = S::BF, NST = fft_stages(C), BIN = S::BIN;
     static_assert(S::OK, "shape not supported by the backward kernel");
     extern __shared__ __align__(128) unsigned char smem[];
     float2* gslot = reinterpret_cast<float2*>(smem);                    // [2][B][C] complex FP32
@@ -83,14 +90,12 @@ __global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(Bwd
     const long long u0 = (long long)blockIdx.x * U / gridDim.x;
     const long long u1 = (long long)(blockIdx.x + 1) * U / gridDim.x;
 
-    // taps of channel c as (h, h) pairs; tap-gradient accumulators (over all segments)
-    unsigned long long hh[TM], acch[TM];
+    // tap-gradient accumulators (over all segments); the taps of channel c are
+    // loaded (from L1) as (h, h) pairs before each batch's channel sums, so
+    // they are not live across the inverse DFT
+    unsigned long long acch[TM];
 #pragma unroll
-    for (int t = 0; t < TM; ++t) {
-        const float h = __ldg(args.taps + t * C + c);
-        hh[t] = pk2(h, h);
-        acch[t] = 0ull;
-    }
+    for (int t = 0; t < TM; ++t) acch[t] = 0ull;
     for (int i = c; i < tw_size(C); i += NT) tw_s[i] = args.tw[i];
     if (c == 0) {
         for (int i = 0; i < 5; ++i) mbar_init(&bars[i], 1);
@@ -182,25 +187,33 @@ __global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(Bwd
                 fft_stage<C, B, NT, decltype(p)::value, OUT_CF32, true, S::SPW, true>(gs, tw_s, nullptr, 0, 0, 0);
             });
             __syncthreads();
-            // one thread per channel: sequence g_i = carried rows (i < TM-1) then the batch rows
-            const long long row0 = j * B;                  // first raw row (and G row) of the batch
-            unsigned long long gxa[B];
+            unsigned long long hh[TM];
 #pragma unroll
-            for (int r = 0; r < B; ++r) gxa[r] = 0ull;
-            unsigned long long gseq[B + TM - 1];
+            for (int t = 0; t < TM; ++t) {
+                const float h = __ldg(args.taps + t * C + c);
+                hh[t] = pk2(h, h);
+            }
+            // one thread per channel, in passes of BF rows: sequence g_i = carried rows
+            // (i < TM-1) then the pass's rows
+            for (int hf = 0; hf < B / BF; ++hf) {
+            const long long row0 = j * B + hf * BF;       // first raw row (and G row) of the pass
+            unsigned long long gxa[BF];
+#pragma unroll
+            for (int r = 0; r < BF; ++r) gxa[r] = 0ull;
+            unsigned long long gseq[BF + TM - 1];
 #pragma unroll
             for (int i = 0; i < TM - 1; ++i) gseq[i] = carry[i];
-            const float2* gsc = gs + c;
-            const unsigned char* xsc = xs + c * BIN;
-            if (row0 + B <= n_spectra && T == TM) {        // whole batch, every tap: no checks
+            const float2* gsc = gs + (size_t)hf * BF * C + c;
+            const unsigned char* xsc = xs + ((size_t)hf * BF * C + c) * BIN;
+            if (row0 + BF <= n_spectra && T == TM) {        // whole batch, every tap: no checks
 #pragma unroll
-                for (int r = 0; r < B; ++r) {
+                for (int r = 0; r < BF; ++r) {
                     const float2 g = gsc[r * C];
                     gseq[TM - 1 + r] = pk2(g.x, g.y);
                 }
                 if (k >= 0) {
 #pragma unroll
-                    for (int r = 0; r < B; ++r) {
+                    for (int r = 0; r < BF; ++r) {
                         const float2 xv = load_one_smem<IN>(xsc + (size_t)r * C * BIN);
                         const unsigned long long xp = pk2(xv.x, xv.y);
 #pragma unroll
@@ -213,18 +226,18 @@ __global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(Bwd
                     if (gx != nullptr) {
                         float2* gxr = gx + (size_t)row0 * C + c;
 #pragma unroll
-                        for (int r = 0; r < B; ++r) gxr[r * C] = upk2(gxa[r]);
+                        for (int r = 0; r < BF; ++r) gxr[r * C] = upk2(gxa[r]);
                     }
                 }
             } else {
 #pragma unroll
-                for (int r = 0; r < B; ++r) {
+                for (int r = 0; r < BF; ++r) {
                     const float2 g = (row0 + r < n_spectra) ? gsc[r * C] : make_float2(0.f, 0.f);
                     gseq[TM - 1 + r] = pk2(g.x, g.y);
                 }
                 if (k >= 0) {
 #pragma unroll
-                    for (int r = 0; r < B; ++r) {
+                    for (int r = 0; r < BF; ++r) {
                         const float2 xv = (row0 + r < n_raw) ? load_one_smem<IN>(xsc + (size_t)r * C * BIN)
                                                              : make_float2(0.f, 0.f);
                         const unsigned long long xp = pk2(xv.x, xv.y);
@@ -240,13 +253,14 @@ __global__ void __launch_bounds__(BwdShape<C, TM, IN>::NT, 1) pfb_bwd_kernel(Bwd
                     if (gx != nullptr) {
                         float2* gxr = gx + (size_t)row0 * C + c;
 #pragma unroll
-                        for (int r = 0; r < B; ++r)
+                        for (int r = 0; r < BF; ++r)
                             if (row0 + r < n_raw) gxr[r * C] = upk2(gxa[r]);
                     }
                 }
             }
 #pragma unroll
-            for (int i = 0; i < TM - 1; ++i) carry[i] = gseq[B + i];
+            for (int i = 0; i < TM - 1; ++i) carry[i] = gseq[BF + i];
+            }
             __syncthreads();
             if (c == 0 && it + 2 < nit) {
                 fence_proxy_async_smem();

@@ -251,6 +251,7 @@ def test_backward_three_pass_shapes(mods, C, T, S, ns, in_dtype):
 
 
 @pytest.mark.parametrize("C,T,S,ns,in_dtype", [(256, 16, 500, 2, "ci8"), (512, 8, 300, 1, "cf32"),
+                                               (512, 8, 700, 2, "ci8"), (512, 3, 51, 3, "ci16"),
                                                (64, 1, 70, 3, "ci16")])
 def test_three_pass_adjoint_matches_fused(mods, C, T, S, ns, in_dtype):
     """Where the fused kernel exists, the three-pass path (forced by the
