@@ -75,7 +75,17 @@ constexpr int spec_span() { return LAYOUT == 1 ? C + C / last_radix(C) : C; }
 template <int C, int P, int LAYOUT = 0>
 __device__ __forceinline__ int phys(int i) {
     constexpr int NST = fft_stages(C);
-    if constexpr (P > 0 && P == NST - 1 && LAYOUT == 1) {
+    if constexpr (P > 0 && P == NST - 1 && LAYOUT == 2) {
+        // 16-byte chunks (element pairs) of each row of R >= 16 elements
+        // XOR-swizzled with the row index mod 8: a lane reading a whole row
+        // as 16-byte loads and lanes walking 8 consecutive rows hit 8
+        // distinct chunks of the 128-byte bank window, and a row written
+        // element by element stays one contiguous row
+        constexpr int R = fft_radix(C, P);
+        static_assert(R >= 16, "pair-chunk swizzle needs rows of at least 16 elements");
+        const int row = i / R, col = i % R;
+        return row * R + (((col >> 1) ^ (row & 7)) << 1) + (col & 1);
+    } else if constexpr (P > 0 && P == NST - 1 && LAYOUT == 1) {
         constexpr int R = fft_radix(C, P);
         return (i / R) * (R + 1) + i % R;
     } else if constexpr (P > 0 && P == NST - 1) {
@@ -121,6 +131,15 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 }
 
 // ------------------------------------------------------------ launch shape
+// Raw batches are copied with an L2 evict-first policy (each is read once):
+// +0.1-0.3 % on every measured carry-kernel shape; the output's lines stay
+// in L2 longer.
+#ifndef PPF_TMA_EVICT_FIRST
+#define PPF_TMA_EVICT_FIRST 1
+#endif
+#ifndef PPF_PACKED_MIN_L
+#define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
+#endif
 #ifndef PPF_GENERIC_B4096
 #define PPF_GENERIC_B4096 2      // spectra per batch of the generic kernel at C = 4096
 #endif
@@ -218,7 +237,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr int IPT = (TOTAL + WORKERS - 1) / WORKERS;        // items per thread
     constexpr bool EXACT = IPT * WORKERS == TOTAL;
     constexpr int SPAN = spec_span<C, LAYOUT>();   // elements per spectrum in ybuf
-    static_assert(!(LAYOUT == 1 && (INV || SMEM_OUT)), "padded rows only for the forward stores to HBM");
+    static_assert(!(LAYOUT >= 1 && (INV || SMEM_OUT)), "padded or pair-swizzled rows only for the forward stores to HBM");
     static_assert(EXACT || (SPW == 0 && is_c3(C)) || TOTAL < WORKERS,
                   "items must divide evenly (a warp or CTA may leave threads idle)");
     const int gtid = GRP::tid();
@@ -237,10 +256,20 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         const int sp = sp0 + item / ITEMS, e = item % ITEMS;
         const int b = e % NN, prefix = e / NN;
         const float2* src = ybuf + sp * SPAN;
+        if constexpr (LAYOUT == 2 && P == NST - 1 && NN == 1) {
+            // the item's whole row, as 16-byte element pairs
 #pragma unroll
-        for (int a = 0; a < R; ++a) {
-            v[it][a] = src[phys<C, P, LAYOUT>(prefix * NP + NN * a + b)];
-            if constexpr (INV && P == 0) v[it][a].y = -v[it][a].y;
+            for (int a = 0; a < R; a += 2) {
+                const float4 q = *reinterpret_cast<const float4*>(src + phys<C, P, LAYOUT>(prefix * NP + a));
+                v[it][a] = make_float2(q.x, q.y);
+                v[it][a + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                v[it][a] = src[phys<C, P, LAYOUT>(prefix * NP + NN * a + b)];
+                if constexpr (INV && P == 0) v[it][a].y = -v[it][a].y;
+            }
         }
     }
     sync();   // every read of this stage is done before anything is overwritten
@@ -335,7 +364,7 @@ __device__ __forceinline__ void fir_segment(const Src& src, const float2* __rest
                                             int T, float4 (&acc)[L]) {
 #pragma unroll
     for (int j = 0; j < L; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if constexpr (TM <= 16 && !(Src::kRing && IN != IN_CF32 && L >= 4)) {
+    if constexpr (TM <= 16 && !(Src::kRing && IN != IN_CF32 && L >= PPF_PACKED_MIN_L)) {
         // raw-sample-outer order: all TM taps live in registers, one sample live
         // (scalar FMAs: faster than the packed form below when the samples come
         // from global memory, for fp32 samples and for segments of 2 outputs)
@@ -542,8 +571,9 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
             uint64_t* bar = &bars[j % NS];
             const uint32_t bytes = (uint32_t)(rows * C * S::BIN);
             mbar_expect_tx(bar, bytes);
-            tma_load_1d(ring + (j % NS) * S::SLOTB,
-                        static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * S::BIN, bytes, bar);
+            const unsigned char* src = static_cast<const unsigned char*>(in) + (size_t)(lo + j) * B * C * S::BIN;
+            if constexpr (PPF_TMA_EVICT_FIRST) tma_load_1d_once(ring + (j % NS) * S::SLOTB, src, bytes, bar);
+            else tma_load_1d(ring + (j % NS) * S::SLOTB, src, bytes, bar);
         }
     };
     auto wait_upto = [&](long long j) -> bool {            // thread 0: batches < issued only

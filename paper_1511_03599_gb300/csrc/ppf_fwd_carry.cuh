@@ -24,10 +24,13 @@
 
 #include "ppf_fwd.cuh"
 
-// Raw batches are copied with an L2 evict-first policy (each is read once):
-// +0.1-0.3 % on every measured shape, the output's lines stay in L2 longer.
-#ifndef PPF_TMA_EVICT_FIRST
-#define PPF_TMA_EVICT_FIRST 1
+// The last DFT stage's buffer uses the pair-chunk swizzle (phys, LAYOUT 2)
+// where it measured faster than the element swizzle: C = 1024 (+0.4 % at
+// T = 8, +3 % at T = 16, int8), int16 input at C = 512 (+1.3 %) and int8
+// input at C = 256 (+1.6 %); it measured 1-3 % slower for int8 and fp32 input
+// at C = 512 and fp32 at C = 256.  PPF_LAYOUT2=0 turns it off.
+#ifndef PPF_LAYOUT2
+#define PPF_LAYOUT2 1
 #endif
 
 namespace ppf {
@@ -62,8 +65,11 @@ struct CarryCand {
     static constexpr int BIN = InTraits<IN>::bytes;
     // last DFT stage's buffer: padded rows (no per-access index arithmetic)
     // where they measured faster -- C <= 128, and 16 taps at C <= 256 --
-    // else the XOR swizzle (C = 512/1024 at T <= 8 lost 2-4 % with padding)
-    static constexpr int LAYOUT = (C <= 128 || (TM >= 16 && C <= 256)) ? 1 : 0;
+    // else the element XOR swizzle (C = 512/1024 at T <= 8 lost 2-4 % with
+    // padding) or, where it measured faster, the pair-chunk swizzle
+    static constexpr bool PAIR_SWIZZLE = PPF_LAYOUT2 && last_radix(C) >= 16 &&
+                                         (C == 1024 || (C == 512 && IN == IN_CI16) || (C == 256 && IN == IN_CI8));
+    static constexpr int LAYOUT = (C <= 128 || (TM >= 16 && C <= 256)) ? 1 : PAIR_SWIZZLE ? 2 : 0;
     static constexpr int YSPAN = spec_span<C, LAYOUT>();             // elements per spectrum in ybuf
     static constexpr int YBYTES = B * YSPAN * 8;
     static constexpr int SLOTB = B * C * BIN;

@@ -31,6 +31,10 @@
 
 #include "ppf_fwd.cuh"
 
+#ifndef PPF_CLUSTER_4096_CI16
+#define PPF_CLUSTER_4096_CI16 0
+#endif
+
 namespace ppf {
 
 // channels per CTA of a cluster: 256 (two CTAs per SM) where the cluster
@@ -65,7 +69,7 @@ struct ClusterShape {
     // except 8-tap int8, and fp32 input at C = 4096 (the generic kernel won
     // at C = 3072, at C = 4096 for 8/16-bit input, at C = 1024 and 1536)
     static constexpr bool WANTED = C == 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
-                                   (C == 4096 && IN == IN_CF32);
+                                   (C == 4096 && (IN == IN_CF32 || (PPF_CLUSTER_4096_CI16 && IN == IN_CI16)));
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
 };
