@@ -1,6 +1,7 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
 // on a thread-block cluster (used where it measured faster than the
-// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input at C = 4096).
+// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input and 5-8-tap
+// int16 input at C = 4096).
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
@@ -31,8 +32,12 @@
 
 #include "ppf_fwd.cuh"
 
+// int16 input at C = 4096 with 5..8 taps: the generic kernel's deep ring
+// does not fit shared memory there (16 KB rows), and the cluster kernel
+// measured 20 % faster than its direct-load mode (113 vs 94 GS/s); with up to
+// 4 taps the ring fits and the generic kernel is faster (229 GS/s).
 #ifndef PPF_CLUSTER_4096_CI16
-#define PPF_CLUSTER_4096_CI16 0
+#define PPF_CLUSTER_4096_CI16 1
 #endif
 
 namespace ppf {
@@ -66,10 +71,11 @@ struct ClusterShape {
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
     // where it measured faster than the single-CTA kernels: C = 2048, C = 768
-    // except 8-tap int8, and fp32 input at C = 4096 (the generic kernel won
-    // at C = 3072, at C = 4096 for 8/16-bit input, at C = 1024 and 1536)
+    // except 8-tap int8, fp32 input at C = 4096 and 8-tap-bucket int16 input
+    // at C = 4096 (the generic kernel won at C = 3072, at C = 4096 for int8
+    // and for int16 with up to 4 taps, at C = 1024 and 1536)
     static constexpr bool WANTED = C == 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
-                                   (C == 4096 && (IN == IN_CF32 || (PPF_CLUSTER_4096_CI16 && IN == IN_CI16)));
+                                   (C == 4096 && (IN == IN_CF32 || (PPF_CLUSTER_4096_CI16 && IN == IN_CI16 && TM == 8)));
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
 };
