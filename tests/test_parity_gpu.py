@@ -92,7 +92,8 @@ def test_parity_non_power_of_two_channels(ppf, C, T, in_dtype, out_dtype):
 # state over several batches.
 @pytest.mark.parametrize("C", [768, 1024, 1536, 2048, 3072, 4096])
 @pytest.mark.parametrize("T,in_dtype,out_dtype", [(8, "ci8", "c64"), (4, "cf32", "c64"), (16, "ci16", "c16"),
-                                                  (1, "ci8", "c64"), (13, "ci8", "c64"), (2, "cf32", "c16")])
+                                                  (1, "ci8", "c64"), (13, "ci8", "c64"), (2, "cf32", "c16"),
+                                                  (8, "ci16", "c64"), (5, "ci16", "c64")])
 def test_parity_cluster_channels(ppf, C, T, in_dtype, out_dtype):
     S = 6 * 152 * 16 // max(1, C // 512) + 7
     h = synth.design_taps(C, T, scale=(1.0 / np.sqrt(C) if out_dtype == "c16" else 1.0))
