@@ -195,7 +195,7 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   (C[i]*T[i] FP32, tap-major; read during the call).  Complex int8 input and
  *   complex FP32 output only (else UNSUPPORTED).  The plan cuts every beam
  *   into tiles of about 2^20 samples, sorts them largest first into a wide
- *   (C >= 2048) and a narrow queue and keeps taps, twiddles, descriptors,
+ *   (C >= 1024) and a narrow queue and keeps taps, twiddles, descriptors,
  *   tiles, two work-queue counters and a status word in device memory it
  *   allocates.  Synchronous.
  * ppf_beams_bind -- the device buffers of every beam (in_dev[i]: C[i]*(n_spectra[i]
@@ -206,14 +206,16 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  * ppf_beams_execute -- enqueue one reset of the two queue counters and ONE
  *   launch of the persistent kernel (one CTA of 512 threads per SM;
  *   ctas_per_sm is accepted for compatibility and clamped to what fits).
- *   Each CTA first pulls wide tiles (beams with C >= 2048) and runs each with
- *   all its threads -- the FIR + DFT body of the single-stream kernel for that
- *   C, raw rows staged through a TMA ring -- then splits into two groups of
- *   256 threads that pull narrow tiles (C <= 1024) independently.  Every
- *   beam's result equals ppf_execute's up to FP32 rounding (bit-identical for
- *   C = 4096).  Asynchronous on `stream`; no allocation.
+ *   Each CTA first pulls wide tiles (beams with C >= 1024) and runs each with
+ *   all its threads, then splits into two groups of 256 threads that pull
+ *   narrow tiles (C <= 512) independently.  A tile runs the FIR + DFT body of
+ *   the single-stream kernel for its C: the carry kernel's at C = 512 and
+ *   1024 (FIR halo carried in registers), the generic kernel's otherwise (raw
+ *   rows staged through a TMA ring).  Every beam's result equals
+ *   ppf_execute's up to FP32 rounding (bit-identical at C = 512, 1024 and
+ *   4096).  Asynchronous on `stream`; no allocation.
  * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=CTAs per SM,
- *   [4]=SMs, [5]=dynamic shared memory bytes, [6]=wide tiles (C >= 2048).
+ *   [4]=SMs, [5]=dynamic shared memory bytes, [6]=wide tiles (C >= 1024).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
  * ppf_beams_destroy -- free everything (NULL accepted).
  * Errors: INVALID_ARG, UNSUPPORTED, ALIGNMENT, CUDA, OUT_OF_MEMORY, DEVICE_TIMEOUT.

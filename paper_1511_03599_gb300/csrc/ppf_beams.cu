@@ -3,14 +3,17 @@
 //
 // The plan cuts every beam into tiles (contiguous ranges of output batches of
 // about `tile_samples` samples) and sorts the tiles largest first in two
-// queues: beams with C >= 2048 ("wide" tiles) and beams with C <= 1024
+// queues: beams with C >= 1024 ("wide" tiles) and beams with C <= 512
 // ("narrow" tiles).  The grid is persistent: one CTA of 512 threads per SM.
 // Each CTA first pulls wide tiles from a device counter and runs each with
-// the whole CTA -- the FIR + DFT body of the single-stream kernel for that C
-// (512 threads, raw rows and their halo staged through a TMA ring).  When the
-// wide queue is empty, the CTA splits into two groups of 256 threads, each
-// with half of the shared memory and its own named barrier, and each group
-// pulls narrow tiles from the second counter and runs them independently.
+// the whole CTA: at C = 1024 the body of the carry kernel (one channel pair
+// per thread, the FIR halo carried in registers, warp-local DFT stages), at
+// C >= 2048 the body of the generic kernel (raw rows and their halo staged
+// through a TMA ring).  When the wide queue is empty, the CTA splits into two
+// groups of 256 threads, each with half of the shared memory and its own
+// named barrier, and each group pulls narrow tiles from the second counter
+// and runs them independently: the carry body at C = 512, the generic body
+// below.
 // Both counters are reset by one memset before the launch, so the pair can
 // be captured in a CUDA graph.  The body of each tile is chosen by the beam's
 // (C, tap bucket) class.  Complex int8 input, complex FP32 output: the
@@ -39,7 +42,7 @@ constexpr int kNarrowThreads = 256;               // a group of a CTA running na
 constexpr int kBeamC[] = {64, 128, 256, 512, 1024, 2048, 4096};
 constexpr int kBeamTM[] = {4, 8, 16};
 constexpr int kNumC = 7, kNumTM = 3;
-constexpr int kFirstWide = 5;                     // kBeamC[5] = 2048: wide from here on
+constexpr int kFirstWide = 4;                     // kBeamC[4] = 1024: wide from here on
 
 struct BeamDesc {
     const void* in;          // C*(S+T-1) complex int8 samples
@@ -65,6 +68,19 @@ struct BeamsArgs {
 };
 
 template <int CI> constexpr int class_threads() { return CI >= kFirstWide ? kBeamThreads : kNarrowThreads; }
+// C = 512 (a half-CTA group) and C = 1024 (the whole CTA): the carry
+// kernel's body, whose one-channel-pair-per-thread shape matches the group;
+// the other classes run fwd_range
+template <int CI, int TI>
+constexpr bool class_carry() {
+    constexpr int C = kBeamC[CI], TM = kBeamTM[TI];
+    if constexpr (C == 512 || C == 1024) {
+        using S = CarryShape<C, TM, IN_CI8>;
+        return S::OK && S::NT == class_threads<CI>();
+    } else {
+        return false;
+    }
+}
 
 template <int CI, int TI, class GRP>
 __device__ __forceinline__ bool beam_tile(const BeamsArgs& a, const BeamDesc& d, const BeamTile& t,
@@ -82,7 +98,10 @@ __device__ __forceinline__ bool beam_tile(const BeamsArgs& a, const BeamDesc& d,
     fa.n_spectra = d.n_spectra;
     fa.T = d.T;
     fa.flags = a.flags;
-    return fwd_range<C, TM, IN_CI8, OUT_CF32, class_threads<CI>(), GRP>(fa, d.in, d.out, t.lo, t.hi, smem);
+    if constexpr (class_carry<CI, TI>())
+        return carry_range<C, TM, IN_CI8, OUT_CF32, false, GRP, true>(fa, d.in, d.out, t.lo, t.hi, smem);
+    else
+        return fwd_range<C, TM, IN_CI8, OUT_CF32, class_threads<CI>(), GRP>(fa, d.in, d.out, t.lo, t.hi, smem);
 }
 
 // run tile t with the body of class cls, among classes with C index in [CI, CEND)
@@ -96,7 +115,10 @@ __device__ __forceinline__ bool beam_dispatch(int cls, const BeamsArgs& a, const
 }
 
 template <int CI, int TI>
-constexpr int class_smem_of() { return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::SMEM; }
+constexpr int class_smem_of() {
+    if constexpr (class_carry<CI, TI>()) return CarryShape<kBeamC[CI], kBeamTM[TI], IN_CI8>::SMEM;
+    else return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::SMEM;
+}
 template <int CI, int TI, int CEND>
 constexpr int class_smem_max() {
     constexpr int s = class_smem_of<CI, TI>();
@@ -106,7 +128,9 @@ constexpr int class_smem_max() {
 }
 template <int CI, int TI>
 constexpr int class_batch(int cls) {
-    if (cls == CI * kNumTM + TI) return FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::B;
+    if (cls == CI * kNumTM + TI)
+        return class_carry<CI, TI>() ? CarryShape<kBeamC[CI], kBeamTM[TI], IN_CI8>::B
+                                     : FwdShape<kBeamC[CI], kBeamTM[TI], IN_CI8, class_threads<CI>()>::B;
     if constexpr (TI + 1 < kNumTM) return class_batch<CI, TI + 1>(cls);
     else if constexpr (CI + 1 < kNumC) return class_batch<CI + 1, 0>(cls);
     else return 0;

@@ -120,41 +120,41 @@ struct CarryShapeSel {
 template <int C, int TM, int IN>
 struct CarryShape : CarryShapeSel<C, TM, IN>::type {};
 
+// The carry kernel's body over output batches [lo, hi) of one stream (in,
+// out: that stream's buffers), run by the thread group GRP of S::NT threads
+// on its shared memory.  MULTI: the group runs several ranges in one launch
+// (the multi-beam kernel): it waits for the group before reusing shared
+// memory, and retires the ring's barriers after the range (every copy has
+// landed by then: each issued batch is waited for) so the next range can
+// initialise them again.  Returns false if a bounded wait gave up.
+//
 // FIRONLY: the unfused ablation -- the FIR alone, writing the filtered
 // spectra y (complex FP32, spectrum-major) to global memory instead of
 // transforming them (the paper's FIR kernel followed by a separate DFT).
-template <int C, int TM, int IN, int OUT, bool FIRONLY = false>
-__global__ void __launch_bounds__(CarryShape<C, TM, IN>::NT, CarryShape<C, TM, IN>::MINB)
-pfb_fwd_carry_kernel(FwdArgs args) {
+template <int C, int TM, int IN, int OUT, bool FIRONLY, class GRP, bool MULTI>
+__device__ __forceinline__ bool carry_range(const FwdArgs& args, const void* in, void* out, long long lo, long long hi,
+                                            unsigned char* smem) {
     using S = CarryShape<C, TM, IN>;
     constexpr int NT = S::NT, B = S::B, BIN = S::BIN;
     constexpr int NST = fft_stages(C);
     static_assert(S::OK, "shape not supported by the carry kernel");
-    extern __shared__ __align__(128) unsigned char smem[];
     float2* ybuf = reinterpret_cast<float2*>(smem);
     float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
     unsigned char* ring = smem + S::RING_OFF;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + 2 * S::SLOTB);     // 3 barriers
     volatile int* sflag = reinterpret_cast<volatile int*>(bars + 3);
 
-    const int tid = threadIdx.x;
+    const int tid = GRP::tid();
     const int cp = tid;                              // channel pair
     const long long n_spectra = args.n_spectra;
     const int T = args.T;
     const int D = TM - T;                            // leading zero taps of the bucket
     const long long n_raw = n_spectra + T - 1;
-    const long long nbt = (n_spectra + B - 1) / B;
-    const int cps = (int)(gridDim.x / args.n_streams);   // CTAs per stream (the grid is a multiple)
-    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
-    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
-    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
-    const long long lo = (long long)bx * nbt / cps;
-    const long long hi = (long long)(bx + 1) * nbt / cps;
     const long long nb = hi - lo;
-    if (nb <= 0) return;
+    if (nb <= 0) return true;
+    if constexpr (MULTI) GRP::sync();                // the group's previous range is done with shared memory
     const long long vlo = lo * B, vhi = (hi * B < n_spectra) ? hi * B : n_spectra;
-    const long long nraw_b = (T > 1) ? nb + 1 : nb;  // raw batches this CTA streams
-
+    const long long nraw_b = (T > 1) ? nb + 1 : nb;  // raw batches this range streams
     auto rows_of = [&](long long j) -> long long {
         const long long r = n_raw - (lo + j) * B;
         return r <= 0 ? 0 : (r < B ? r : B);
@@ -182,6 +182,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
         for (int i = 0; i < 3; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
         *sflag = 0;
+        if constexpr (MULTI) fence_proxy_async_smem();   // the slots were last read by the previous range
         if (EARLY) {
             issue(0);
             if (nraw_b > 1) issue(1);
@@ -213,7 +214,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    __syncthreads();
+    GRP::sync();
     if (!EARLY && tid == 0) {
         issue(0);
         if (nraw_b > 1) issue(1);
@@ -233,8 +234,8 @@ pfb_fwd_carry_kernel(FwdArgs args) {
                 *sflag = 1;
             }
         }
-        __syncthreads();
-        if (*sflag) return;
+        GRP::sync();
+        if (*sflag) return false;
         // ---------------------------------------------------------- FIR
         // sequence x_i: i < TM-1 carried rows, then the B rows of slot k.
         // output j = sum_{t < TM} h'[t] x_{j+t}
@@ -282,7 +283,7 @@ pfb_fwd_carry_kernel(FwdArgs args) {
                 }
             }
         }
-        __syncthreads();
+        GRP::sync();
         // slot k is free: refill it with raw batch k+2
         if (tid == 0 && k + 2 < nraw_b) {
             fence_proxy_async_smem();
@@ -292,11 +293,33 @@ pfb_fwd_carry_kernel(FwdArgs args) {
         if constexpr (!FIRONLY) {
             const long long sb = (lo + k) * B - (T - 1);     // output spectrum of batch row 0
             static_for<NST>([&](auto p) {
-                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW, false, false, S::LAYOUT>(
+                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, S::SPW, false, false, S::LAYOUT, GRP>(
                     ybuf, tws, out, sb, vlo, vhi);
             });
         }
     }
+    if constexpr (MULTI) {
+        GRP::sync();                                 // every thread is past its last wait
+        if (tid == 0)
+            for (int i = 0; i < 3; ++i) mbar_inval(&bars[i]);
+    }
+    return true;
+}
+
+template <int C, int TM, int IN, int OUT, bool FIRONLY = false>
+__global__ void __launch_bounds__(CarryShape<C, TM, IN>::NT, CarryShape<C, TM, IN>::MINB)
+pfb_fwd_carry_kernel(FwdArgs args) {
+    using S = CarryShape<C, TM, IN>;
+    constexpr int B = S::B, BIN = S::BIN;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const long long nbt = (args.n_spectra + B - 1) / B;
+    const int cps = (int)(gridDim.x / args.n_streams);   // CTAs per stream (the grid is a multiple)
+    const int strm = blockIdx.x / cps, bx = blockIdx.x - strm * cps;
+    const void* in = static_cast<const unsigned char*>(args.in) + (size_t)strm * args.in_stride * BIN;
+    void* out = static_cast<unsigned char*>(args.out) + (size_t)strm * args.out_stride * (OUT == OUT_CF32 ? 8 : 4);
+    const long long lo = (long long)bx * nbt / cps;
+    const long long hi = (long long)(bx + 1) * nbt / cps;
+    carry_range<C, TM, IN, OUT, FIRONLY, CtaGroup, false>(args, in, out, lo, hi, smem);
 }
 
 }  // namespace ppf
