@@ -209,11 +209,11 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   Each CTA first pulls wide tiles (beams with C >= 1024) and runs each with
  *   all its threads, then splits into two groups of 256 threads that pull
  *   narrow tiles (C <= 512) independently.  A tile runs the FIR + DFT body of
- *   the single-stream kernel for its C: the carry kernel's at C = 512 and
- *   1024 (FIR halo carried in registers), the generic kernel's otherwise (raw
- *   rows staged through a TMA ring).  Every beam's result equals
- *   ppf_execute's up to FP32 rounding (bit-identical at C = 512, 1024 and
- *   4096).  Asynchronous on `stream`; no allocation.
+ *   a single-stream kernel: the carry kernel's at C = 1024 (FIR halo carried
+ *   in registers), the generic kernel's otherwise (raw rows staged through a
+ *   TMA ring).  Every beam's result equals ppf_execute's up to FP32 rounding
+ *   (bit-identical at C = 1024 and 4096, where ppf_execute runs the same
+ *   body).  Asynchronous on `stream`; no allocation.
  * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=CTAs per SM,
  *   [4]=SMs, [5]=dynamic shared memory bytes, [6]=wide tiles (C >= 1024).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.

@@ -12,8 +12,7 @@
 // through a TMA ring).  When the wide queue is empty, the CTA splits into two
 // groups of 256 threads, each with half of the shared memory and its own
 // named barrier, and each group pulls narrow tiles from the second counter
-// and runs them independently: the carry body at C = 512, the generic body
-// below.
+// and runs them independently with the generic body.
 // Both counters are reset by one memset before the launch, so the pair can
 // be captured in a CUDA graph.  The body of each tile is chosen by the beam's
 // (C, tap bucket) class.  Complex int8 input, complex FP32 output: the
@@ -34,6 +33,13 @@
 #include "../../include/ppf.h"
 #include "ppf_fwd.cuh"
 #include "ppf_internal.h"
+
+// C = 512 tiles on the carry body of a half-CTA group measured 2 % slower on
+// the C <= 512 beams of the 96-beam set than on fwd_range (and equal on the
+// whole set), so they run fwd_range unless this is set.
+#ifndef PPF_BEAMS_CARRY512
+#define PPF_BEAMS_CARRY512 0
+#endif
 
 namespace ppf {
 
@@ -68,13 +74,13 @@ struct BeamsArgs {
 };
 
 template <int CI> constexpr int class_threads() { return CI >= kFirstWide ? kBeamThreads : kNarrowThreads; }
-// C = 512 (a half-CTA group) and C = 1024 (the whole CTA): the carry
-// kernel's body, whose one-channel-pair-per-thread shape matches the group;
-// the other classes run fwd_range
+// C = 1024 (the whole CTA): the carry kernel's body, whose
+// one-channel-pair-per-thread shape matches the group; the other classes
+// run fwd_range
 template <int CI, int TI>
 constexpr bool class_carry() {
     constexpr int C = kBeamC[CI], TM = kBeamTM[TI];
-    if constexpr (C == 512 || C == 1024) {
+    if constexpr ((C == 512 && PPF_BEAMS_CARRY512) || C == 1024) {
         using S = CarryShape<C, TM, IN_CI8>;
         return S::OK && S::NT == class_threads<CI>();
     } else {

@@ -137,6 +137,9 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 #ifndef PPF_TMA_EVICT_FIRST
 #define PPF_TMA_EVICT_FIRST 1
 #endif
+#ifndef PPF_PINGPONG
+#define PPF_PINGPONG 0
+#endif
 #ifndef PPF_PACKED_MIN_L
 #define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
 #endif
@@ -169,8 +172,14 @@ struct FwdShape {
     static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
     static constexpr int NS = HS + 2;                                // ring slots
     static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
-    static constexpr bool TW_SMEM = YBYTES + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
-    static constexpr int RING_OFF = YBYTES + (TW_SMEM ? TWBYTES : 0);
+    // two filtered-spectra buffers where they fit beside the ring, for 512
+    // threads: the DFT stages then run out of place (read one buffer, write
+    // the other), one CTA barrier per stage instead of two
+    static constexpr bool PINGPONG = PPF_PINGPONG && NT == 512 &&
+                                     2 * YBYTES + (RING ? NS * SLOTB + 64 : 0) <= CTA_SMEM_MAX;
+    static constexpr int YB = PINGPONG ? 2 * YBYTES : YBYTES;        // bytes of the spectra buffers
+    static constexpr bool TW_SMEM = YB + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
+    static constexpr int RING_OFF = YB + (TW_SMEM ? TWBYTES : 0);
     static constexpr int SMEM = RING_OFF + (RING ? NS * SLOTB + 64 : 0);
     // each thread keeps one channel pair for the whole run: taps stay in registers
     static constexpr bool TAPS_IN_REGS = (FPT == 1) && (TM <= 16) && (NT % PAIRS == 0);
@@ -223,9 +232,10 @@ struct HalfGroup {
 // its last stage writes the result back into the spectrum's own row of
 // ybuf in natural order instead of to global memory.
 template <int C, int B, int NT, int P, int OUT, bool TW_SMEM, int SPW = 0, bool INV = false, bool SMEM_OUT = false,
-          int LAYOUT = 0, class GRP = CtaGroup>
+          int LAYOUT = 0, class GRP = CtaGroup, bool OOP = false>
 __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float2* __restrict__ tws,
-                                          void* __restrict__ out, long long sb, long long vlo, long long vhi) {
+                                          void* __restrict__ out, long long sb, long long vlo, long long vhi,
+                                          float2* __restrict__ dbuf = nullptr) {
     constexpr int NST = fft_stages(C);
     constexpr int R = fft_radix(C, P);
     constexpr int NP = fft_n(C, P);
@@ -238,6 +248,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
     constexpr bool EXACT = IPT * WORKERS == TOTAL;
     constexpr int SPAN = spec_span<C, LAYOUT>();   // elements per spectrum in ybuf
     static_assert(!(LAYOUT >= 1 && (INV || SMEM_OUT)), "padded or pair-swizzled rows only for the forward stores to HBM");
+    static_assert(!(OOP && (INV || SMEM_OUT || SPW > 0)), "out-of-place stages only for the CTA-wide forward");
     static_assert(EXACT || (SPW == 0 && is_c3(C)) || TOTAL < WORKERS,
                   "items must divide evenly (a warp or CTA may leave threads idle)");
     const int gtid = GRP::tid();
@@ -272,7 +283,11 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
             }
         }
     }
-    sync();   // every read of this stage is done before anything is overwritten
+    // every read of this stage is done before anything is overwritten; OOP
+    // (out of place): a non-last stage writes to dbuf, a last stage stores to
+    // global memory, and the caller orders the buffer's next writer after
+    // these reads with a barrier of its own
+    if constexpr (!OOP) sync();
 #pragma unroll
     for (int it = 0; it < IPT; ++it) {
         const int item = wid + it * WORKERS;
@@ -282,7 +297,7 @@ __device__ __forceinline__ void fft_stage(float2* __restrict__ ybuf, const float
         dft_reg<R>(v[it]);
         if constexpr (P + 1 < NST) {
             apply_twiddles<R, NN, TW_SMEM>(v[it], tws + tw_offset(C, P), b);
-            float2* dst = ybuf + sp * SPAN;
+            float2* dst = (OOP ? dbuf : ybuf) + sp * SPAN;
 #pragma unroll
             for (int k = 0; k < R; ++k) dst[phys<C, P + 1, LAYOUT>((prefix + PP * k) * NN + b)] = v[it][k];
         } else if constexpr (INV) {
@@ -530,7 +545,8 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
     constexpr int NST = fft_stages(C);
     constexpr bool RING = S::RING;
     float2* ybuf = reinterpret_cast<float2*>(smem);
-    float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
+    float2* ybuf2 = reinterpret_cast<float2*>(smem + S::YBYTES);        // PINGPONG only
+    float2* tw_s = reinterpret_cast<float2*>(smem + S::YB);
     unsigned char* ring = smem + S::RING_OFF;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + NS * S::SLOTB);   // NS + 1 barriers
     volatile int* sflag = reinterpret_cast<volatile int*>(bars + NS + 1);
@@ -657,10 +673,22 @@ __device__ __forceinline__ bool fwd_range(const FwdArgs& args, const void* in, v
             }
         }
         // ---------------------------------------------------------- FFT
-        static_for<NST>([&](auto p) {
-            fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, 0, false, false, 0, GRP>(ybuf, tws, out, sb, 0,
-                                                                                              n_spectra);
-        });
+        if constexpr (S::PINGPONG) {
+            // stage p reads buffer p & 1 and writes buffer (p + 1) & 1; the last
+            // stage's reads are ordered before the next batch's FIR writes by the
+            // barrier after the ring wait, or by the one below without a ring
+            static_for<NST>([&](auto p) {
+                constexpr int P = decltype(p)::value;
+                fft_stage<C, B, NT, P, OUT, S::TW_SMEM, 0, false, false, 0, GRP, true>(
+                    (P & 1) ? ybuf2 : ybuf, tws, out, sb, 0, n_spectra, (P & 1) ? ybuf : ybuf2);
+            });
+            if constexpr (!RING) GRP::sync();
+        } else {
+            static_for<NST>([&](auto p) {
+                fft_stage<C, B, NT, decltype(p)::value, OUT, S::TW_SMEM, 0, false, false, 0, GRP>(ybuf, tws, out, sb, 0,
+                                                                                                  n_spectra);
+            });
+        }
     }
     if constexpr (RING) {
         // every copy of the range has landed (thread 0 waited for each):
