@@ -138,7 +138,7 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 #define PPF_TMA_EVICT_FIRST 1
 #endif
 #ifndef PPF_PINGPONG
-#define PPF_PINGPONG 0
+#define PPF_PINGPONG 1
 #endif
 #ifndef PPF_PACKED_MIN_L
 #define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
@@ -172,11 +172,12 @@ struct FwdShape {
     static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
     static constexpr int NS = HS + 2;                                // ring slots
     static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
-    // two filtered-spectra buffers where they fit beside the ring, for 512
-    // threads: the DFT stages then run out of place (read one buffer, write
-    // the other), one CTA barrier per stage instead of two
-    static constexpr bool PINGPONG = PPF_PINGPONG && NT == 512 &&
-                                     2 * YBYTES + (RING ? NS * SLOTB + 64 : 0) <= CTA_SMEM_MAX;
+    // direct-load mode with 512 threads: two filtered-spectra buffers, so the
+    // DFT stages run out of place (read one buffer, write the other), one CTA
+    // barrier per stage instead of two (C = 3072 fp32: 93 -> 133 GS/s); with
+    // the ring the second buffer would push the twiddles out of shared
+    // memory, which measured 1 % slower at C = 4096
+    static constexpr bool PINGPONG = PPF_PINGPONG && NT == 512 && !RING && 2 * YBYTES <= CTA_SMEM_MAX;
     static constexpr int YB = PINGPONG ? 2 * YBYTES : YBYTES;        // bytes of the spectra buffers
     static constexpr bool TW_SMEM = YB + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YB + (TW_SMEM ? TWBYTES : 0);
