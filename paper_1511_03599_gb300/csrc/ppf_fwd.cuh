@@ -140,6 +140,9 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 #ifndef PPF_PINGPONG
 #define PPF_PINGPONG 1
 #endif
+#ifndef PPF_PINGPONG_256
+#define PPF_PINGPONG_256 1       // also for 256 threads at C = 1536 (fp32 +43 %; C = 768 lost 1.5 %)
+#endif
 #ifndef PPF_PACKED_MIN_L
 #define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
 #endif
@@ -172,12 +175,14 @@ struct FwdShape {
     static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
     static constexpr int NS = HS + 2;                                // ring slots
     static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
-    // direct-load mode with 512 threads: two filtered-spectra buffers, so the
-    // DFT stages run out of place (read one buffer, write the other), one CTA
-    // barrier per stage instead of two (C = 3072 fp32: 93 -> 133 GS/s); with
-    // the ring the second buffer would push the twiddles out of shared
-    // memory, which measured 1 % slower at C = 4096
-    static constexpr bool PINGPONG = PPF_PINGPONG && NT == 512 && !RING && 2 * YBYTES <= CTA_SMEM_MAX;
+    // direct-load mode with 512 threads (and at C = 1536 with 256): two
+    // filtered-spectra buffers, so the DFT stages run out of place (read one
+    // buffer, write the other), one CTA barrier per stage instead of two
+    // (fp32 at C = 3072: 93 -> 131 GS/s, at C = 1536: 94 -> 135); with the
+    // ring the second buffer would push the twiddles out of shared memory,
+    // which measured 1 % slower at C = 4096
+    static constexpr bool PINGPONG = PPF_PINGPONG && (NT == 512 || (PPF_PINGPONG_256 && C >= 1536)) && !RING &&
+                                     2 * YBYTES <= CTA_SMEM_MAX;
     static constexpr int YB = PINGPONG ? 2 * YBYTES : YBYTES;        // bytes of the spectra buffers
     static constexpr bool TW_SMEM = YB + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YB + (TW_SMEM ? TWBYTES : 0);
