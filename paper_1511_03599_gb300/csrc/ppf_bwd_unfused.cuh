@@ -85,7 +85,8 @@ struct AdjFirArgs {
 };
 
 constexpr int kAdjL = 8;     // raw rows per grad_x tile
-constexpr int kAdjTB = 16;   // taps per grad_h block
+constexpr int kAdjStage = 8; // rows (or taps) each thread has in flight through its staging slots
+constexpr int kAdjTB = 8;    // taps per grad_h block
 
 // Complex pair (2 channels) as (re0, re1) and (im0, im1) packed registers.
 __device__ __forceinline__ void load_gpair(const float2* __restrict__ row, int p, bool ok, unsigned long long& re,
@@ -95,11 +96,29 @@ __device__ __forceinline__ void load_gpair(const float2* __restrict__ row, int p
     im = pk2(v.y, v.w);
 }
 
-// grid.x: tiles (grid-stride over n_streams * ceil(n_raw / kAdjL)), grid.y: blocks of channel pairs.
+// Asynchronous 4/8/16-byte copy global -> shared (the thread's own staging
+// slot), committed in groups; wait_group<N> returns once at most N of the
+// thread's most recent groups are still in flight.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// grid.x: tiles (grid-stride over n_streams * ceil(n_raw / kAdjL)), grid.y: blocks of channel pairs.  Each thread
+// streams the g_y rows its taps bring in, and the taps, through kAdjStage
+// shared-memory staging slots of its own (cp.async), kAdjStage taps ahead.
 static __global__ void __launch_bounds__(128) pfb_bwd_gradx_kernel(AdjFirArgs a) {
-    constexpr int L = kAdjL;
+    constexpr int L = kAdjL, D = kAdjStage;
+    static_assert(L % D == 0, "staging slots repeat within a tap block");
+    __shared__ __align__(16) float4 sg[D][128];                      // g_y pair of a staged row
+    __shared__ __align__(8) float2 sh[D][128];                       // taps of the pair for a staged tap
     const int C = a.C, T = a.T;
-    const int p = blockIdx.y * blockDim.x + threadIdx.x;     // channel pair
+    const int tl = threadIdx.x;
+    const int p = blockIdx.y * blockDim.x + tl;                      // channel pair
     if (p >= C / 2) return;
     const long long S = a.n_spectra, n_raw = S + T - 1;
     const long long tiles = (n_raw + L - 1) / L;
@@ -107,6 +126,20 @@ static __global__ void __launch_bounds__(128) pfb_bwd_gradx_kernel(AdjFirArgs a)
     for (long long u = blockIdx.x; u < tiles * a.n_streams; u += gridDim.x) {
         const long long strm = u / tiles, r0 = (u - strm * tiles) * L;
         const float2* g = a.gy + (size_t)strm * S * C;
+        // tap t (>= 1) brings row r0 - t (zero outside the stream) and h[t]
+        // into staging slot (t - 1) mod D, requested D taps ahead
+        auto stage = [&](int t) {
+            if (t < T) {
+                const int slot = (t - 1) % D;
+                const long long r = r0 - t;
+                if (r >= 0 && r < S) cp_async<16>(&sg[slot][tl], g + (size_t)r * C + 2 * p);
+                else sg[slot][tl] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cp_async<8>(&sh[slot][tl], taps2 + (size_t)t * (C / 2) + p);
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int d = 1; d <= D; ++d) stage(d);
         // slot m mod L holds g_y row r0 + m; at tap t output j reads row r0 + j - t
         unsigned long long wr[L], wi[L], ar[L], ai[L];
 #pragma unroll
@@ -115,17 +148,26 @@ static __global__ void __launch_bounds__(128) pfb_bwd_gradx_kernel(AdjFirArgs a)
             load_gpair(g + (size_t)r * C, p, r < S, wr[j], wi[j]);
             ar[j] = ai[j] = 0ull;
         }
+        unsigned long long hh;
+        {
+            const float2 h = __ldg(taps2 + p);
+            hh = pk2(h.x, h.y);
+        }
         for (int tb = 0; tb < T; tb += L) {
 #pragma unroll
             for (int v = 0; v < L; ++v) {
                 const int t = tb + v;
                 if (t < T) {
                     if (t > 0) {                                 // row r0 - t enters slot (-t) mod L
-                        const long long r = r0 - t;
-                        load_gpair(g + (size_t)r * C, p, r >= 0 && r < S, wr[(L - v) % L], wi[(L - v) % L]);
+                        const int slot = (v + L - 1) % D;        // (t - 1) mod D
+                        cp_async_wait<D - 1>();
+                        const float4 gv = sg[slot][tl];
+                        wr[(L - v) % L] = pk2(gv.x, gv.z);
+                        wi[(L - v) % L] = pk2(gv.y, gv.w);
+                        const float2 h = sh[slot][tl];
+                        hh = pk2(h.x, h.y);
+                        stage(t + D);
                     }
-                    const float2 h = __ldg(taps2 + (size_t)t * (C / 2) + p);
-                    const unsigned long long hh = pk2(h.x, h.y);
 #pragma unroll
                     for (int j = 0; j < L; ++j) {
                         ffma2(ar[j], hh, wr[(j - v + L) % L]);
@@ -134,6 +176,7 @@ static __global__ void __launch_bounds__(128) pfb_bwd_gradx_kernel(AdjFirArgs a)
                 }
             }
         }
+        cp_async_wait<0>();
         float4* out = reinterpret_cast<float4*>(a.gx + (size_t)strm * a.gx_stride);
 #pragma unroll
         for (int j = 0; j < L; ++j) {
@@ -154,14 +197,21 @@ struct AdjCorrArgs {
     int C, T, TM, n_parts;
 };
 
+
 // grid.x: parts of the rows of all streams, grid.y: blocks of channel pairs,
-// grid.z: blocks of kAdjTB taps.
+// grid.z: blocks of kAdjTB taps.  Each thread streams its rows through kAdjStage
+// shared-memory staging slots of its own (cp.async), so kAdjStage rows of g_y and x
+// are in flight while it works on the oldest.
 template <int IN>
-__global__ void __launch_bounds__(128) pfb_bwd_gradh_kernel(AdjCorrArgs a) {
-    constexpr int TB = kAdjTB, BIN = InTraits<IN>::bytes;
+__global__ void __launch_bounds__(128, 4) pfb_bwd_gradh_kernel(AdjCorrArgs a) {
+    constexpr int TB = kAdjTB, BIN = InTraits<IN>::bytes, XB = 2 * BIN, D = kAdjStage;
+    static_assert(TB % D == 0 || D % TB == 0, "staging slots and window slots repeat together");
+    __shared__ __align__(16) float4 sg[D][128];                      // g_y pair of a staged row
+    __shared__ __align__(16) unsigned char sx[D][128 * XB];          // x pair of a staged row
     const int C = a.C, T = a.T;
-    const int p = blockIdx.y * blockDim.x + threadIdx.x;     // channel pair
-    if (p >= C / 2) return;
+    const int tl = threadIdx.x;
+    const int p = blockIdx.y * blockDim.x + tl;                      // channel pair
+    const bool active = p < C / 2;
     const int t0 = blockIdx.z * TB;
     const long long S = a.n_spectra, n_raw = S + T - 1;
     const long long R = S * a.n_streams;
@@ -170,30 +220,54 @@ __global__ void __launch_bounds__(128) pfb_bwd_gradh_kernel(AdjCorrArgs a) {
     unsigned long long acc[TB];
 #pragma unroll
     for (int v = 0; v < TB; ++v) acc[v] = 0ull;
-    while (u < u1) {                                          // segments of single streams
+    auto unpack_x = [&](const unsigned char* q, unsigned long long& re, unsigned long long& im) {
+        const float4 v = load_pair_smem<IN>(q);
+        re = pk2(v.x, v.z);
+        im = pk2(v.y, v.w);
+    };
+    while (active && u < u1) {                                        // segments of single streams
         const long long strm = u / S, s0 = u - strm * S;
         const long long s1 = (u1 - strm * S < S) ? u1 - strm * S : S;
         u = strm * S + s1;
         const float2* g = a.gy + (size_t)strm * S * C;
         const unsigned char* x = static_cast<const unsigned char*>(a.x) + (size_t)strm * a.x_stride * BIN;
+        // stage row s: g_y row s and the x row entering the window there, s + t0 + TB - 1
+        auto stage = [&](long long s, int slot) {
+            if (s < s1) {
+                cp_async<16>(&sg[slot][tl], g + (size_t)s * C + 2 * p);
+                const long long r = s + t0 + TB - 1;
+                if (r < n_raw) {
+                    cp_async<XB>(&sx[slot][tl * XB], x + ((size_t)r * C + 2 * p) * BIN);
+                } else {
+                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    memcpy(&sx[slot][tl * XB], &z, XB);
+                }
+            }
+            cp_async_commit();
+        };
         // slot m mod TB holds x row s0 + t0 + m (re pair, im pair); at row s0 + i,
         // tap t0 + v reads row s0 + i + t0 + v, slot (i + v) mod TB
         unsigned long long xr[TB], xi[TB];
-        auto load_x = [&](long long r, unsigned long long& re, unsigned long long& im) {
-            const float4 v = r < n_raw ? load_pair_global<IN>(x, r * C + 2 * p) : make_float4(0.f, 0.f, 0.f, 0.f);
-            re = pk2(v.x, v.z);
-            im = pk2(v.y, v.w);
-        };
 #pragma unroll
-        for (int m = 0; m + 1 < TB; ++m) load_x(s0 + t0 + m, xr[m], xi[m]);
+        for (int m = 0; m + 1 < TB; ++m) {
+            const long long r = s0 + t0 + m;
+            const float4 v = r < n_raw ? load_pair_global<IN>(x, r * C + 2 * p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xr[m] = pk2(v.x, v.z);
+            xi[m] = pk2(v.y, v.w);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) stage(s0 + d, d);
         for (long long ib = 0; ib < s1 - s0; ib += TB) {
 #pragma unroll
             for (int i = 0; i < TB; ++i) {
                 const long long s = s0 + ib + i;
                 if (s < s1) {
-                    load_x(s + t0 + TB - 1, xr[(i + TB - 1) % TB], xi[(i + TB - 1) % TB]);
-                    unsigned long long gr, gi;
-                    load_gpair(g + (size_t)s * C, p, true, gr, gi);
+                    const int slot = i % D;                           // (s - s0) mod D
+                    cp_async_wait<D - 1>();                           // row s has landed
+                    const float4 gv = sg[slot][tl];
+                    const unsigned long long gr = pk2(gv.x, gv.z), gi = pk2(gv.y, gv.w);
+                    unpack_x(&sx[slot][tl * XB], xr[(i + TB - 1) % TB], xi[(i + TB - 1) % TB]);
+                    stage(s + D, slot);
 #pragma unroll
                     for (int v = 0; v < TB; ++v) {
                         ffma2(acc[v], gr, xr[(i + v) % TB]);
@@ -202,7 +276,9 @@ __global__ void __launch_bounds__(128) pfb_bwd_gradh_kernel(AdjCorrArgs a) {
                 }
             }
         }
+        cp_async_wait<0>();
     }
+    if (!active) return;
     float* part = a.partials + (size_t)blockIdx.x * a.TM * C;
 #pragma unroll
     for (int v = 0; v < TB; ++v) {
