@@ -14,11 +14,15 @@
 //      to the scratch;
 //   2. pfb_bwd_gradx_kernel: one thread per channel pair and tile of kAdjL
 //      raw rows, taps outermost with a window of kAdjL g_y rows in registers
-//      (one new row per tap);
+//      (one new row per tap, with its tap, staged kAdjStage taps ahead);
 //   3. pfb_bwd_gradh_kernel<IN>: one thread per channel pair, block of
 //      kAdjTB taps and part of the rows of all streams, a window of kAdjTB
-//      x rows in registers (one new row per row); per-part partial sums
-//      reduced in a fixed order by pfb_bwd_reduce_kernel (deterministic).
+//      x rows in registers (one new x row and one g_y row per row, staged
+//      kAdjStage rows ahead); per-part partial sums reduced in a fixed order
+//      by pfb_bwd_reduce_kernel (deterministic).
+// The staging: each thread copies the rows it will need with cp.async into
+// shared-memory slots of its own and waits for the oldest group, so several
+// global loads are in flight per thread without holding registers.
 // HBM traffic per raw sample is about G 8 + g_y 8 (write) + g_y 8 + grad_x 8
 // + g_y 8 + x; the halo and tap-block re-reads come from L2.
 #pragma once
