@@ -100,18 +100,6 @@ __device__ __forceinline__ void load_gpair(const float2* __restrict__ row, int p
     im = pk2(v.y, v.w);
 }
 
-// Asynchronous 4/8/16-byte copy global -> shared (the thread's own staging
-// slot), committed in groups; wait_group<N> returns once at most N of the
-// thread's most recent groups are still in flight.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "n"(BYTES)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 // grid.x: tiles (grid-stride over n_streams * ceil(n_raw / kAdjL)), grid.y: blocks of channel pairs.  Each thread
 // streams the g_y rows its taps bring in, and the taps, through kAdjStage
 // shared-memory staging slots of its own (cp.async), kAdjStage taps ahead.

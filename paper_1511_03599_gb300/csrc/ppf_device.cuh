@@ -358,6 +358,18 @@ __device__ __forceinline__ void tma_prefetch_l2(const void* src_gmem, uint32_t b
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
 }
 
+// Asynchronous 4/8/16-byte copy global -> shared (the thread's own staging
+// slot), committed in groups; wait_group<N> returns once at most N of the
+// thread's most recent groups are still in flight.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst_smem, const void* src_gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Bulk copy shared -> global through the async proxy (bulk-group completion).
 // dst, src and bytes must be multiples of 16.  The writing threads make their
 // shared-memory stores visible to the async proxy (fence_proxy_async_smem)

@@ -23,6 +23,10 @@
 
 #include "ppf_fwd_carry.cuh"
 
+#ifndef PPF_LONGTAP_STAGE
+#define PPF_LONGTAP_STAGE 1
+#endif
+
 namespace ppf {
 
 template <int C, int IN>
@@ -39,7 +43,15 @@ struct LongShape {
     static constexpr int CHUNKB = RC * C * BIN;
     static constexpr int RING_OFF = YBYTES + TWBYTES;
     static constexpr int BAR_OFF = RING_OFF + NS * CHUNKB;           // NS full + NS empty + 1 + flag
-    static constexpr int SMEM = BAR_OFF + 8 * (2 * NS + 2);
+    // STAGE: each thread's taps stream through TD shared-memory slots of its
+    // own (cp.async, TD taps ahead) instead of a rolling set of registers --
+    // where it measured faster: C = 512 with int16 (+3 .. +10 %) or fp32 input
+    // (+12 .. +13 %); for int8 at C = 512 (-6 % at T = 17, 32; +4 % at T = 64)
+    // and at C = 256 (-8 .. -13 %) the registers stay
+    static constexpr bool STAGE = PPF_LONGTAP_STAGE != 0 && C == 512 && IN != IN_CI8;
+    static constexpr int TD = 8;
+    static constexpr int TAP_OFF = BAR_OFF + 8 * (2 * NS + 2);
+    static constexpr int SMEM = TAP_OFF + (STAGE ? TD * NT * 8 : 0);
     static constexpr bool OK = C >= 64 && C <= 512 && NT % 32 == 0 && SPW >= 1 && SPW * NWARP == B &&
                                warp_fft_ok(C, SPW) && SMEM <= 226 * 1024 && B % RC == 0;
 };
@@ -51,6 +63,7 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
     constexpr int NST = fft_stages(C);
     constexpr int OB = OUT == OUT_CF32 ? 8 : 4;
     static_assert(S::OK, "shape not supported by the long-tap kernel");
+    static_assert(!S::STAGE || B % S::TD == 0, "a tap's staging slot is its index in the block mod TD");
     extern __shared__ __align__(128) unsigned char smem[];
     float2* ybuf = reinterpret_cast<float2*>(smem);
     float2* tw_s = reinterpret_cast<float2*>(smem + S::YBYTES);
@@ -59,6 +72,7 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
     uint64_t* empty = full + NS;                                         // [NS] every warp is done with it
     uint64_t* inj = full + 2 * NS;                                       // never completed (testing aid)
     volatile int* sdead = reinterpret_cast<volatile int*>(full + 2 * NS + 1);
+    float2* stap = reinterpret_cast<float2*>(smem + S::TAP_OFF);          // [TD][NT] staged taps (STAGE)
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int cp = tid;
@@ -136,6 +150,16 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
         if (lane == 0) mbar_arrive_cta(&empty[slot]);
     };
 
+    // STAGE: tap t of the pair goes to the thread's slot t mod TD; one commit
+    // group per tap (an empty group past the last tap), so a wait for all
+    // but the TD-1 youngest groups means "tap t has landed"
+    const float2* tp = taps2 + cp;
+    auto stage_tap = [&](int t) {
+        if constexpr (S::STAGE) {
+            if (t < T) cp_async<8>(&stap[(t % S::TD) * NT + tid], tp + (size_t)t * (C / 2));
+            cp_async_commit();
+        }
+    };
     BatchShare share(nbt, args.n_streams, blockIdx.x, gridDim.x);
     long long strm, lo, hi;
     bool first = true;
@@ -154,6 +178,8 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
         first = false;
         __syncthreads();
 
+#pragma unroll
+        for (int t = 0; t < S::TD; ++t) stage_tap(t);                 // the first batch's first taps
         for (long long k = lo; k < hi; ++k) {
             const long long g0 = g_base + (k - lo) * nch;      // first chunk use of this batch
             const int s0 = (int)(g0 % NS), q0 = (int)((g0 / NS) & 1);
@@ -184,14 +210,16 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
                 release(sl);
                 if (tid == 0 && !*sdead) refill(g0 + c + 1 + NS);
             }
-            // taps 4 ahead in a rolling set of registers (tap t lives in hq[t % 4]); the
-            // plan pads the tap table with zero rows, so loads past T stay in bounds
-            const float2* tp = taps2 + cp;
+            // without STAGE: taps 4 ahead in a rolling set of registers (tap t lives in
+            // hq[t % 4]); the plan pads the tap table with zero rows, so loads past T
+            // stay in bounds
             unsigned long long hq[4];
+            if constexpr (!S::STAGE) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float2 h = __ldg(tp + i * (C / 2));
-                hq[i] = pk2(h.x, h.y);
+                for (int i = 0; i < 4; ++i) {
+                    const float2 h = __ldg(tp + i * (C / 2));
+                    hq[i] = pk2(h.x, h.y);
+                }
             }
             // taps in blocks of B: tap t = tb + u uses window slot (j + u) mod B for output j,
             // then slot u takes row t + B, in chunk (t + B) / RC, at row (t + B) mod RC = u mod RC.
@@ -212,8 +240,14 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
                 for (int u = 0; u < B; ++u) {
                     const int t = tb + u;
                     if (FULL || t < T) {
-                        const unsigned long long h = hq[u % 4];
-                        {
+                        unsigned long long h;
+                        if constexpr (S::STAGE) {
+                            cp_async_wait<S::TD - 1>();              // tap t has landed
+                            const float2 hv = stap[(u % S::TD) * NT + tid];   // t mod TD (tb is a multiple of B)
+                            h = pk2(hv.x, hv.y);
+                            stage_tap(t + S::TD);
+                        } else {
+                            h = hq[u % 4];
                             const float2 hn = __ldg(tp + (t + 4) * (C / 2));
                             hq[u % 4] = pk2(hn.x, hn.y);
                         }
@@ -240,6 +274,10 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
                 const float2 r = upk2(acc[j][0]), im = upk2(acc[j][1]);
                 *reinterpret_cast<float4*>(ybuf + j * C + 2 * cp) = make_float4(r.x, im.x, r.y, im.y);
             }
+            if (k + 1 < hi) {                                        // the next batch's first taps land
+#pragma unroll                                                       // during this batch's DFT
+                for (int t = 0; t < S::TD; ++t) stage_tap(t);
+            }
             __syncthreads();
             // ------------------------------------------------------------- FFT
             const long long vhi = *sdead ? 0 : n_spectra;           // a CTA that gave up stores nothing
@@ -251,6 +289,7 @@ __global__ void __launch_bounds__(LongShape<C, IN>::NT, 1) pfb_fwd_longtap_kerne
         g_base = seg_end;
     }
     // leave only after every copy this CTA issued has landed
+    if constexpr (S::STAGE) cp_async_wait<0>();
     if (tid == 0)
         for (long long g = (issued > NS ? issued - NS : 0); g < issued; ++g)
             mbar_wait_bounded(&full[g % NS], (uint32_t)((g / NS) & 1), kWaitLimitNs);
