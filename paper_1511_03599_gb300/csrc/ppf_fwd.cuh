@@ -146,6 +146,9 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 #ifndef PPF_PACKED_MIN_L
 #define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
 #endif
+#ifndef PPF_GENERIC_B2048
+#define PPF_GENERIC_B2048 4      // spectra per batch of the generic kernel at C = 2048
+#endif
 #ifndef PPF_GENERIC_B4096
 #define PPF_GENERIC_B4096 2      // spectra per batch of the generic kernel at C = 4096
 #endif
@@ -154,7 +157,7 @@ struct FwdShape {
     static constexpr int NT = NTO ? NTO : (C >= 2048 ? 512 : 256);   // threads per CTA
     static constexpr int PAIRS = C / 2;
     // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k)
-    static constexpr int B = (C >= 4096) ? PPF_GENERIC_B4096 : (C >= 2048) ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
+    static constexpr int B = (C >= 4096) ? PPF_GENERIC_B4096 : (C >= 2048) ? PPF_GENERIC_B2048 : is_c3(C) ? 16 * 384 / C : 8192 / C;
     // large-T FIR order (see fir_segment): tap chunks for narrow input at C <= 512
     static constexpr bool CHUNK = TM > 16 && IN != IN_CF32 && C <= 512;
     static constexpr int L0 = (TM >= 32 && !CHUNK) ? 8 : 16;

@@ -36,6 +36,9 @@
 // does not fit shared memory there (16 KB rows), and the cluster kernel
 // measured 20 % faster than its direct-load mode (113 vs 94 GS/s); with up to
 // 4 taps the ring fits and the generic kernel is faster (229 GS/s).
+#ifndef PPF_CLUSTER_2048
+#define PPF_CLUSTER_2048 1
+#endif
 #ifndef PPF_CLUSTER_4096_CI16
 #define PPF_CLUSTER_4096_CI16 1
 #endif
@@ -74,7 +77,7 @@ struct ClusterShape {
     // except 8-tap int8, fp32 input at C = 4096 and 8-tap-bucket int16 input
     // at C = 4096 (the generic kernel won at C = 3072, at C = 4096 for int8
     // and for int16 with up to 4 taps, at C = 1024 and 1536)
-    static constexpr bool WANTED = C == 2048 || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
+    static constexpr bool WANTED = (C == 2048 && PPF_CLUSTER_2048) || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
                                    (C == 4096 && (IN == IN_CF32 || (PPF_CLUSTER_4096_CI16 && IN == IN_CI16 && TM == 8)));
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
