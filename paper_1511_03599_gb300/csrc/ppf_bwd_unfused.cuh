@@ -38,12 +38,13 @@ struct IdftArgs {
     long long n_spectra, gY_stride, n_streams;
 };
 
-// Same threads and batch as the forward's generic kernel for C, so the DFT
-// stages divide their items exactly as there.
+// Threads and batch of the forward's generic kernel in its plain
+// configuration (for these its DFT stages divide their items exactly):
+// 64 KB of spectra per batch (48 KB for C = 384/768/1536, 96 KB at 3072).
 template <int C>
 struct IdftShape {
-    static constexpr int NT = FwdShape<C, 1, IN_CF32>::NT;
-    static constexpr int B = FwdShape<C, 1, IN_CF32>::B;
+    static constexpr int NT = C >= 2048 ? 512 : 256;
+    static constexpr int B = C >= 4096 ? 2 : C >= 2048 ? 4 : is_c3(C) ? 16 * 384 / C : 8192 / C;
     static constexpr int YBYTES = B * C * 8;
     static constexpr int SMEM = YBYTES + tw_size(C) * 8;
 };

@@ -146,18 +146,83 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[R], const float2* __r
 #ifndef PPF_PACKED_MIN_L
 #define PPF_PACKED_MIN_L 4       // shortest FIR segment that takes the packed channel-pair path
 #endif
+#ifndef PPF_WIDE_1024
+#define PPF_WIDE_1024 1          // 512 threads (one CTA per SM) for fp32 input at C = 1024, T = 9..16
+#endif
+#ifndef PPF_RING_TIGHT
+#define PPF_RING_TIGHT 1         // a ring of HS + 1 slots where only that fits beside the batch
+#endif
 #ifndef PPF_GENERIC_B2048
-#define PPF_GENERIC_B2048 4      // spectra per batch of the generic kernel at C = 2048
+#define PPF_GENERIC_B2048 0      // spectra per batch of the generic kernel at C = 2048 (0: chosen below)
+#endif
+#ifndef PPF_GENERIC_B1024_SHORT
+#define PPF_GENERIC_B1024_SHORT 4   // spectra per batch at C = 1024, 16/32-bit input, up to 4 taps
+#endif
+#ifndef PPF_GENERIC_B3072
+#define PPF_GENERIC_B3072 4      // spectra per batch of the generic kernel at C = 3072
 #endif
 #ifndef PPF_GENERIC_B4096
-#define PPF_GENERIC_B4096 2      // spectra per batch of the generic kernel at C = 4096
+#define PPF_GENERIC_B4096 0      // spectra per batch of the generic kernel at C = 4096 (0: chosen below)
 #endif
+// Largest dynamic shared memory of one generic-kernel CTA (two CTAs per SM
+// with 256 threads, one with 512).
+constexpr int generic_smem_cap(int NT) { return (NT == 256 ? 113 * 1024 : 226 * 1024) - 128; }
+// Whether the direct-load mode can run its DFT stages out of place between
+// two spectra buffers (512 threads, or 256 from C = 1536).
+constexpr bool generic_pingpong_ok(int C, int B, int NT) {
+    return PPF_PINGPONG && (NT == 512 || (PPF_PINGPONG_256 && C >= 1536)) && 2 * B * C * 8 <= generic_smem_cap(NT);
+}
+// Whether a ring without the refill slot is allowed: where the halo spans two
+// or more batches, or where the alternative is plain direct loads (no
+// out-of-place mode).  A 2-slot ring lost to the out-of-place mode (C = 3072
+// int16 T = 4: 160 vs 170 GS/s) but beat plain direct loads (C = 1024 fp32
+// T = 4: 218 vs 175).
+constexpr bool generic_ring_tight_ok(int C, int TM, int B, int NT) {
+    return PPF_RING_TIGHT && (TM - 1 > B || !generic_pingpong_ok(C, B, NT));
+}
+// Whether the generic kernel's TMA ring fits one CTA's shared memory beside a
+// B-spectrum batch of filtered values: HS = ceil((T-1)/B) halo slots (1 when
+// T-1 <= B) plus the slot being read and, where room is left, one of slack
+// for the refill (`slack` = 1), else none (0).  The ring also needs the FIR
+// segment to cover the whole batch when the halo spans several batches
+// (segments of min(B, 16) outputs at these channel counts, T <= 16).
+constexpr bool generic_ring_fits(int C, int TM, int bin, int B, int NT, int slack) {
+    const int hs = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;
+    const bool one_segment = B <= 16 && TM <= 16;
+    return (TM - 1 <= B || one_segment) && B * C * 8 + (hs + 1 + slack) * B * C * bin + 64 <= generic_smem_cap(NT);
+}
+constexpr bool generic_ring_fits_any(int C, int TM, int bin, int B, int NT) {
+    return generic_ring_fits(C, TM, bin, B, NT, 1) ||
+           (generic_ring_tight_ok(C, TM, B, NT) && generic_ring_fits(C, TM, bin, B, NT, 0));
+}
+// Spectra per batch of the generic kernel at C = 2048 and 4096: the larger
+// batch where its ring fits (fewer halo rows re-read and fewer barriers per
+// spectrum: C = 2048 int8 T = 8, 8 spectra: 265 GS/s vs 213 with 4;
+// C = 4096 int8 T = 8, 4 spectra: 235 vs 184 with 2), else the smaller one
+// where that keeps the ring (C = 4096 int8 T = 16: 128 GS/s with a 10-slot
+// ring of 2-spectrum batches vs 113 without a ring at 4), else the larger
+// (C = 4096 int16 T = 16, direct loads: 105 vs 62).  Beyond 16 taps (no
+// ring at these sizes) the smaller batch, with its out-of-place DFT stages.
+constexpr int generic_batch_large(int C, int TM, int bin, int NT) {
+    const int big = C >= 4096 ? 4 : 8;
+    return TM > 16 ? big / 2
+         : generic_ring_fits_any(C, TM, bin, big, NT) ? big
+         : generic_ring_fits_any(C, TM, bin, big / 2, NT) ? big / 2 : big;
+}
+
 template <int C, int TM, int IN, int NTO = 0>
 struct FwdShape {
-    static constexpr int NT = NTO ? NTO : (C >= 2048 ? 512 : 256);   // threads per CTA
+    // threads per CTA: 512 from C = 2048, and for fp32 input at C = 1024 with
+    // 9-16 taps (out-of-place DFT stages: 149 vs 123 GS/s at T = 16)
+    static constexpr int NT = NTO ? NTO : (C >= 2048 || (C == 1024 && IN == IN_CF32 && TM == 16 && PPF_WIDE_1024)) ? 512 : 256;
     static constexpr int PAIRS = C / 2;
-    // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k)
-    static constexpr int B = (C >= 4096) ? PPF_GENERIC_B4096 : (C >= 2048) ? PPF_GENERIC_B2048 : is_c3(C) ? 16 * 384 / C : 8192 / C;
+    // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k),
+    // 64-128 KB at C = 2048 and 4096 (generic_batch_large)
+    static constexpr int B = (C == 4096) ? (PPF_GENERIC_B4096 ? PPF_GENERIC_B4096 : generic_batch_large(C, TM, InTraits<IN>::bytes, NT))
+                           : (C == 2048) ? (PPF_GENERIC_B2048 ? PPF_GENERIC_B2048 : generic_batch_large(C, TM, InTraits<IN>::bytes, NT))
+                           : C == 3072 ? PPF_GENERIC_B3072
+                           : (C == 1024 && IN != IN_CI8 && TM <= 4) ? PPF_GENERIC_B1024_SHORT
+                           : is_c3(C) ? 16 * 384 / C : 8192 / C;
     // large-T FIR order (see fir_segment): tap chunks for narrow input at C <= 512
     static constexpr bool CHUNK = TM > 16 && IN != IN_CF32 && C <= 512;
     static constexpr int L0 = (TM >= 32 && !CHUNK) ? 8 : 16;
@@ -170,13 +235,17 @@ struct FwdShape {
     static constexpr int TWBYTES = tw_size(C) * 8;
     static constexpr int BIN = InTraits<IN>::bytes;
     static constexpr int SLOTB = B * C * BIN;                        // raw bytes of one batch
-    static constexpr int CTA_SMEM_MAX = (NT == 256 ? 113 * 1024 : 226 * 1024) - 128;
+    static constexpr int CTA_SMEM_MAX = generic_smem_cap(NT);
     // TMA ring: every raw batch is copied into shared memory once; the FIR of
     // batch k reads slot k and the T-1 halo rows from the HS slots after it
     // (HS = 1 when T-1 <= B; a deeper ring where the halo spans several
     // batches -- large C, where B is small -- and one segment covers the batch).
     static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
-    static constexpr int NS = HS + 2;                                // ring slots
+    // ring slots: HS + 2 (one batch of slack for the refill), or HS + 1 where
+    // only that fits (the refill of the slot freed by batch k's FIR then has
+    // batch k's DFT stages to land before batch k+1's FIR reads it)
+    static constexpr int NS = (YBYTES + (HS + 2) * SLOTB + 64 > CTA_SMEM_MAX && generic_ring_tight_ok(C, TM, B, NT) &&
+                               YBYTES + (HS + 1) * SLOTB + 64 <= CTA_SMEM_MAX) ? HS + 1 : HS + 2;
     static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
     // direct-load mode with 512 threads (and at C = 1536 with 256): two
     // filtered-spectra buffers, so the DFT stages run out of place (read one
@@ -184,8 +253,7 @@ struct FwdShape {
     // (fp32 at C = 3072: 93 -> 131 GS/s, at C = 1536: 94 -> 135); with the
     // ring the second buffer would push the twiddles out of shared memory,
     // which measured 1 % slower at C = 4096
-    static constexpr bool PINGPONG = PPF_PINGPONG && (NT == 512 || (PPF_PINGPONG_256 && C >= 1536)) && !RING &&
-                                     2 * YBYTES <= CTA_SMEM_MAX;
+    static constexpr bool PINGPONG = generic_pingpong_ok(C, B, NT) && !RING;
     static constexpr int YB = PINGPONG ? 2 * YBYTES : YBYTES;        // bytes of the spectra buffers
     static constexpr bool TW_SMEM = YB + (RING ? NS * SLOTB + 64 : 0) + TWBYTES <= CTA_SMEM_MAX;
     static constexpr int RING_OFF = YB + (TW_SMEM ? TWBYTES : 0);

@@ -1,7 +1,6 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
 // on a thread-block cluster (used where it measured faster than the
-// single-CTA kernels: C = 2048, most C = 768 shapes, fp32 input and 5-8-tap
-// int16 input at C = 4096).
+// single-CTA kernels: fp32 input at C = 2048, most C = 768 shapes).
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
@@ -32,15 +31,20 @@
 
 #include "ppf_fwd.cuh"
 
-// int16 input at C = 4096 with 5..8 taps: the generic kernel's deep ring
-// does not fit shared memory there (16 KB rows), and the cluster kernel
-// measured 20 % faster than its direct-load mode (113 vs 94 GS/s); with up to
-// 4 taps the ring fits and the generic kernel is faster (229 GS/s).
+// Where the generic kernel measured faster, the cluster kernel is not used:
+// for 8/16-bit input at C = 2048 (int8 T=8: 265 GS/s with 8-spectrum batches
+// vs 202; int16 T=8: 212 vs 170) and at C = 4096 (int16 T=8, a ring of HS + 1
+// slots beside 2-spectrum batches: 173 vs 113; fp32 T=8, 4-spectrum batches
+// loaded directly: 117 vs 104, T=4: 144 vs 116).  fp32 input at C = 2048
+// keeps it (T=8: 158 vs 145 GS/s).  The switches below restore it elsewhere.
 #ifndef PPF_CLUSTER_2048
-#define PPF_CLUSTER_2048 1
+#define PPF_CLUSTER_2048 0
 #endif
-#ifndef PPF_CLUSTER_4096_CI16
-#define PPF_CLUSTER_4096_CI16 1
+#ifndef PPF_CLUSTER_CF32
+#define PPF_CLUSTER_CF32 1       // fp32 input at C = 2048
+#endif
+#ifndef PPF_CLUSTER_4096
+#define PPF_CLUSTER_4096 0       // fp32 input and 5-8-tap int16 input at C = 4096
 #endif
 
 namespace ppf {
@@ -73,12 +77,12 @@ struct ClusterShape {
     static constexpr int TW_OFF = 3 * YLB;
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
-    // where it measured faster than the single-CTA kernels: C = 2048, C = 768
-    // except 8-tap int8, fp32 input at C = 4096 and 8-tap-bucket int16 input
-    // at C = 4096 (the generic kernel won at C = 3072, at C = 4096 for int8
-    // and for int16 with up to 4 taps, at C = 1024 and 1536)
-    static constexpr bool WANTED = (C == 2048 && PPF_CLUSTER_2048) || (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
-                                   (C == 4096 && (IN == IN_CF32 || (PPF_CLUSTER_4096_CI16 && IN == IN_CI16 && TM == 8)));
+    // where it measured faster than the single-CTA kernels: fp32 input at
+    // C = 2048, C = 768 except 8-tap int8 (the generic kernel won at C = 1024,
+    // 1536, 3072 and 4096, and for 8/16-bit input at C = 2048)
+    static constexpr bool WANTED = (C == 2048 && ((IN == IN_CF32 && PPF_CLUSTER_CF32) || PPF_CLUSTER_2048)) ||
+                                   (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
+                                   (C == 4096 && PPF_CLUSTER_4096 && (IN == IN_CF32 || (IN == IN_CI16 && TM == 8)));
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
 };

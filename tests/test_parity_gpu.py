@@ -110,13 +110,17 @@ def test_parity_cluster_channels(ppf, C, T, in_dtype, out_dtype):
 
 
 @pytest.mark.parametrize("C", [768, 1024, 2048, 3072, 4096])
-def test_parity_cluster_every_output_batched(ppf, C):
-    """Several independent streams in one launch (strided), every output compared."""
+@pytest.mark.parametrize("in_dtype", ["ci8", "cf32"])
+def test_parity_cluster_every_output_batched(ppf, C, in_dtype):
+    """Several independent streams in one launch (strided), every output compared
+    (the cluster kernel for fp32 input at C = 2048, the generic kernel at C = 4096)."""
     T, n_streams = 8, 3
     S = 300
     h = synth.design_taps(C, T)
-    xs = [synth.stream(C, S + T - 1, "ci8", 16.0, 5100 + C + i) for i in range(n_streams)]
-    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
+    xs = [synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5100 + C + i) for i in range(n_streams)]
+    with ppf.Plan(C, T, h, in_dtype, "c64") as plan:
+        if C in (2048, 4096):
+            assert bool(plan.info()["variant"] & 16) == (C == 2048 and in_dtype == "cf32")
         got = plan.execute(torch.stack([to_device(x) for x in xs]), n_streams=n_streams)
         torch.cuda.synchronize()
         got = got.cpu().numpy().astype(np.complex128)
@@ -329,17 +333,21 @@ def test_sweep_cells_sampled(ppf, T, in_dtype, out_dtype):
     check_errors(f"sweep C=512 T={T} S=2^18 {in_dtype}->{out_dtype}", got, ref, out_dtype)
 
 
-@pytest.mark.parametrize("C", [512, 2048])
-def test_bounded_wait_timeout_reported_and_context_usable(ppf, C):
-    """A wait that nothing completes runs out, is reported, and the next launch is correct
-    (C=2048: every CTA of each cluster gives up and the cluster leaves together)."""
+@pytest.mark.parametrize("C,in_dtype,body", [(512, "ci8", "carry"), (2048, "cf32", "cluster"), (2048, "ci8", "ring")])
+def test_bounded_wait_timeout_reported_and_context_usable(ppf, C, in_dtype, body):
+    """A wait that nothing completes runs out, is reported, and the next launch is correct,
+    in each TMA-staged body: the carry kernel, the cluster kernel (every CTA of each cluster
+    gives up and the cluster leaves together) and the generic kernel's ring."""
     T, S = 8, 4096
     h = synth.design_taps(C, T)
-    x = synth.stream(C, S + T - 1, "ci8", 16.0, 12)
+    sigma = {"ci8": 16.0, "cf32": 1.0}[in_dtype]
+    x = synth.stream(C, S + T - 1, in_dtype, sigma, 12)
     xd = to_device(x)
-    with ppf.Plan(C, T, h, "ci8", "c64") as plan:
-        assert plan.info()["variant"] & 1, "expected the TMA-staged kernel for this shape"
-        assert bool(plan.info()["variant"] & 16) == (C >= 2048)
+    with ppf.Plan(C, T, h, in_dtype, "c64") as plan:
+        v = plan.info()["variant"]
+        assert v & 1, "expected the TMA-staged kernel for this shape"
+        # bit 2: FIR halo carried in registers (carry and cluster kernels); bit 4: cluster
+        assert bool(v & 4) == (body != "ring") and bool(v & 16) == (body == "cluster")
         plan.set_debug_flags(1)
         plan(xd)
         with pytest.raises(ppf.PPFError) as ei:
