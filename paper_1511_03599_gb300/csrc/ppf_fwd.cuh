@@ -3,12 +3,13 @@
 // One persistent CTA loops over batches of B consecutive output spectra.
 // Per batch:
 //   1. FIR (Alg. 1): each thread owns a channel pair and a segment of L
-//      output spectra; it streams the L+T-1 raw samples of its pair from
-//      global memory (each raw sample is converted to FP32 once per segment
-//      and reused by all T taps in registers; the T-1 spectra shared with
-//      the neighbouring segment -- the halo of Sec. 3.2 -- come from L2),
-//      and writes the filtered spectra y to shared memory.  y never goes to
-//      global memory.
+//      output spectra; it reads the L+T-1 raw samples of its pair from the
+//      TMA ring of raw batches in shared memory (where the ring fits beside
+//      the batch; else straight from global memory, warmed in L2 ahead) --
+//      each raw sample is converted to FP32 once per segment and reused by
+//      all T taps in registers, the T-1 rows shared with the previous
+//      segment (the halo of Sec. 3.2) are read again -- and writes the
+//      filtered spectra y to shared memory.  y never goes to global memory.
 //   2. DFT (Eq. 2) of every filtered spectrum, C = R_0 * R_1 * ... as a
 //      sequence of stages.  Stage p does R_p-point DFTs in registers on
 //      columns of stride N_{p+1} = N_p / R_p, multiplies by the twiddles

@@ -1,6 +1,6 @@
 // ppf_fwd_cluster.cuh -- fused PFB forward kernel for large channel counts
 // on a thread-block cluster (used where it measured faster than the
-// single-CTA kernels: fp32 input at C = 2048, most C = 768 shapes).
+// single-CTA kernels: fp32 input at C = 768 and 2048).
 //
 // The FIR state of a C-channel stream (T-1 carried rows per channel) does not
 // fit one SM at these sizes, so a cluster of Q = C/KS CTAs shares a stream
@@ -36,7 +36,10 @@
 // vs 202; int16 T=8: 212 vs 170) and at C = 4096 (int16 T=8, a ring of HS + 1
 // slots beside 2-spectrum batches: 173 vs 113; fp32 T=8, 4-spectrum batches
 // loaded directly: 117 vs 104, T=4: 144 vs 116).  fp32 input at C = 2048
-// keeps it (T=8: 158 vs 145 GS/s).  The switches below restore it elsewhere.
+// keeps it (T=8: 158 vs 145 GS/s), and so does fp32 input at C = 768 (T=8:
+// 139 vs 109), where 8/16-bit input now runs faster on the generic kernel's
+// ring (int8 T=16: 142 vs 116; int16 T=8: 167 vs 154).  The switches below
+// restore it elsewhere.
 #ifndef PPF_CLUSTER_2048
 #define PPF_CLUSTER_2048 0
 #endif
@@ -45,6 +48,9 @@
 #endif
 #ifndef PPF_CLUSTER_4096
 #define PPF_CLUSTER_4096 0       // fp32 input and 5-8-tap int16 input at C = 4096
+#endif
+#ifndef PPF_CLUSTER_768
+#define PPF_CLUSTER_768 1        // fp32 input at C = 768
 #endif
 
 namespace ppf {
@@ -78,10 +84,10 @@ struct ClusterShape {
     static constexpr int RING_OFF = TW_OFF + (TW_SMEM ? tw_size(C) * 8 : 0);
     static constexpr int SMEM = RING_OFF + 2 * SLOTB + 64;
     // where it measured faster than the single-CTA kernels: fp32 input at
-    // C = 2048, C = 768 except 8-tap int8 (the generic kernel won at C = 1024,
-    // 1536, 3072 and 4096, and for 8/16-bit input at C = 2048)
+    // C = 768 and 2048 (the generic kernel won at C = 1024, 1536, 3072 and
+    // 4096, and for 8/16-bit input at C = 768 and 2048)
     static constexpr bool WANTED = (C == 2048 && ((IN == IN_CF32 && PPF_CLUSTER_CF32) || PPF_CLUSTER_2048)) ||
-                                   (C == 768 && !(IN == IN_CI8 && TM <= 8)) ||
+                                   (C == 768 && PPF_CLUSTER_768 && IN == IN_CF32) ||
                                    (C == 4096 && PPF_CLUSTER_4096 && (IN == IN_CF32 || (IN == IN_CI16 && TM == 8)));
     static constexpr bool OK = WANTED && C % KS == 0 && Q >= 2 && Q <= 8 && TM <= 16 && B >= TM - 1 &&
                                SPC * C == B * KS && SMEM <= CAP;
