@@ -208,13 +208,16 @@ constexpr int generic_batch_large(int C, int TM, int bin, int NT) {
     const int big = C >= 4096 ? 4 : 8;
     return TM > 16 ? big / 2
          : generic_ring_fits_any(C, TM, bin, big, NT) ? big
-         : generic_ring_fits_any(C, TM, bin, big / 2, NT) ? big / 2 : big;
+         : generic_ring_fits_any(C, TM, bin, big / 2, NT) ? big / 2
+         : big * C * 8 <= generic_smem_cap(NT) ? big : big / 2;
 }
 
 template <int C, int TM, int IN, int NTO = 0>
 struct FwdShape {
     // threads per CTA: 512 from C = 2048, and for fp32 input at C = 1024 with
     // 9-16 taps (out-of-place DFT stages: 149 vs 123 GS/s at T = 16)
+    // (two CTAs of 256 threads per SM at C = 2048/3072, on half the batch,
+    // measured slower: 256 vs 265 GS/s at C = 2048 int8 T = 8, 133 vs 152 at 3072)
     static constexpr int NT = NTO ? NTO : (C >= 2048 || (C == 1024 && IN == IN_CF32 && TM == 16 && PPF_WIDE_1024)) ? 512 : 256;
     static constexpr int PAIRS = C / 2;
     // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k),
@@ -243,10 +246,15 @@ struct FwdShape {
     // batches -- large C, where B is small -- and one segment covers the batch).
     static constexpr int HS = TM - 1 <= B ? 1 : (TM - 1 + B - 1) / B;    // halo slots
     // ring slots: HS + 2 (one batch of slack for the refill), or HS + 1 where
-    // only that fits (the refill of the slot freed by batch k's FIR then has
-    // batch k's DFT stages to land before batch k+1's FIR reads it)
-    static constexpr int NS = (YBYTES + (HS + 2) * SLOTB + 64 > CTA_SMEM_MAX && generic_ring_tight_ok(C, TM, B, NT) &&
-                               YBYTES + (HS + 1) * SLOTB + 64 <= CTA_SMEM_MAX) ? HS + 1 : HS + 2;
+    // only that fits, or where only that leaves room for the twiddle table
+    // (the refill of the slot freed by batch k's FIR then has batch k's DFT
+    // stages to land before batch k+1's FIR reads it; twiddles in shared
+    // memory beside a 2-slot ring measured +2 .. +3 % at C = 2048 and 4096)
+    static constexpr bool NS_TIGHT_FITS = YBYTES + (HS + 1) * SLOTB + 64 <= CTA_SMEM_MAX;
+    static constexpr bool NS_TIGHT_FOR_TW = YBYTES + (HS + 2) * SLOTB + 64 + TWBYTES > CTA_SMEM_MAX &&
+                                            YBYTES + (HS + 1) * SLOTB + 64 + TWBYTES <= CTA_SMEM_MAX;
+    static constexpr int NS = (generic_ring_tight_ok(C, TM, B, NT) && NS_TIGHT_FITS &&
+                               (YBYTES + (HS + 2) * SLOTB + 64 > CTA_SMEM_MAX || NS_TIGHT_FOR_TW)) ? HS + 1 : HS + 2;
     static constexpr bool RING = (TM - 1 <= B || (G == 1 && TM <= 16)) && (YBYTES + NS * SLOTB + 64 <= CTA_SMEM_MAX);
     // direct-load mode with 512 threads (and at C = 1536 with 256): two
     // filtered-spectra buffers, so the DFT stages run out of place (read one
@@ -263,6 +271,7 @@ struct FwdShape {
     static constexpr bool TAPS_IN_REGS = (FPT == 1) && (TM <= 16) && (NT % PAIRS == 0);
     static_assert(FPT >= 1 && (FIR_EXACT || is_c3(C)), "FIR items must divide evenly");
     static_assert(SLOTB % 16 == 0 && YBYTES % 16 == 0 && TWBYTES % 16 == 0, "16-byte alignment");
+    static_assert(SMEM <= CTA_SMEM_MAX, "the batch and its ring must fit one CTA's shared memory");
 };
 
 enum FwdFlags { FWD_INJECT_TIMEOUT = 1 };

@@ -134,7 +134,8 @@ def test_parity_cluster_every_output_batched(ppf, C, in_dtype):
 # kernels): bit-identical to one launch per stream, and right by the oracle.
 @pytest.mark.parametrize("C,T,in_dtype,S,ns", [(512, 8, "ci8", 2000, 5), (256, 16, "cf32", 1500, 7),
                                                (4096, 16, "cf32", 400, 3), (2048, 8, "ci8", 700, 4),
-                                               (64, 1, "ci16", 3000, 9)])
+                                               (64, 1, "ci16", 3000, 9), (4096, 8, "ci8", 301, 3),
+                                               (2048, 16, "ci8", 333, 3), (1024, 4, "cf32", 777, 5)])
 def test_batched_shares_cross_streams(ppf, C, T, in_dtype, S, ns):
     h = synth.design_taps(C, T)
     xs = [synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5200 + C + i) for i in range(ns)]
@@ -151,11 +152,15 @@ def test_batched_shares_cross_streams(ppf, C, T, in_dtype, S, ns):
 
 
 @pytest.mark.parametrize("C,T,in_dtype", [(512, 8, "ci8"), (4096, 4, "ci8"), (1536, 8, "cf32"),
-                                          (384, 8, "ci8"), (32, 4, "ci8"), (4096, 2, "ci8")])
+                                          (384, 8, "ci8"), (32, 4, "ci8"), (4096, 2, "ci8"),
+                                          (4096, 8, "ci8"), (2048, 8, "ci8"), (1024, 4, "cf32"),
+                                          (384, 8, "ci16")])
 def test_more_streams_than_resident_ctas(ppf, C, T, in_dtype):
     """400 short streams in one launch: several waves of carry CTAs, or shares of
     the cluster / generic kernels spanning many streams (the generic kernel in its
-    TMA-ring mode at C=384, 32 and 4096 with T <= 2); bit-identical per stream."""
+    TMA-ring mode at C=32, 384, 1024, 2048 and 4096, with the ring's refill slot
+    (C=2048, T=8) and without it (C=4096, T=8; C=1024 and 384, 16/32-bit input));
+    bit-identical per stream."""
     ns, S = 400, 5
     h = synth.design_taps(C, T)
     x = np.stack([synth.stream(C, S + T - 1, in_dtype, SIGMA[in_dtype], 5300 + i) for i in range(ns)])
