@@ -212,8 +212,8 @@ ppf_status ppf_update_taps(ppf_plan_t plan, const float* taps_dev, ppf_stream_t 
  *   a single-stream kernel: the carry kernel's at C = 1024 (FIR halo carried
  *   in registers), the generic kernel's otherwise (raw rows staged through a
  *   TMA ring).  Every beam's result equals ppf_execute's up to FP32 rounding
- *   (bit-identical at C = 1024 and 4096, where ppf_execute runs the same
- *   body).  Asynchronous on `stream`; no allocation.
+ *   (bit-identical at C = 1024 with up to 8 taps and at C = 4096, where
+ *   ppf_execute runs the same body).  Asynchronous on `stream`; no allocation.
  * ppf_beams_info -- info[0]=beams, [1]=tiles, [2]=tile samples, [3]=CTAs per SM,
  *   [4]=SMs, [5]=dynamic shared memory bytes, [6]=wide tiles (C >= 1024).
  * ppf_beams_check_device -- as ppf_check_device, for the multi-beam launch.
@@ -235,9 +235,10 @@ ppf_status ppf_beams_destroy(ppf_beams_t beams);
  * then a batched FFT library call, Sec. 3.2).
  *   ppf_fir: the FIR alone (Alg. 1): in_dev as for ppf_execute, y_dev
  *            receives n_spectra*C complex FP32 filtered samples y[s][c].
- *            Exists where the fused kernel carries its halo in registers:
+ *            Exists where the carry kernel's FIR fits (halo in registers):
  *            C in {64, 128, 256, 512} (and 1024 for int8 input), T <= 16
- *            (else UNSUPPORTED).
+ *            (else UNSUPPORTED); at C = 1024 with 9-16 taps the fused path
+ *            itself runs the generic kernel.
  *   ppf_fft: the DFT alone (Eq. 2) of n_spectra rows of C complex FP32 values
  *            at y_dev into out_dev (the plan's output type); runs the fused
  *            kernel with T = 1 and unit taps (exact); its internal plan is

@@ -848,9 +848,19 @@ struct FwdInfo {
 
 namespace ppf {
 
+// The carry kernel where it fits, except at C = 1024 with 9-16 taps: its 512
+// threads get at most 128 registers for a carried state estimated at 192,
+// and the generic kernel's ring (two CTAs per SM) measured faster there
+// (int8 T = 16: 247 vs 203 GS/s).  The multi-beam kernel and the FIR-only
+// ablation keep the carry body for those shapes.
+template <int C, int TM, int IN>
+constexpr bool carry_preferred() {
+    return CarryShape<C, TM, IN>::OK && !(C == 1024 && TM > 8);
+}
+
 template <int C, int TM, int IN, int OUT>
 inline FwdInfo fwd_info() {
-    if constexpr (CarryShape<C, TM, IN>::OK) {
+    if constexpr (carry_preferred<C, TM, IN>()) {
         using S = CarryShape<C, TM, IN>;
         return FwdInfo{S::NT, S::B, S::SMEM, fft_stages(C), TM, 1 | (S::TW_SMEM ? 2 : 0) | 4,
                        reinterpret_cast<const void*>(&pfb_fwd_carry_kernel<C, TM, IN, OUT>), 0};
@@ -876,7 +886,7 @@ inline FwdInfo fwd_info() {
 // grid: CTAs (a multiple of the cluster size for cluster kernels).
 template <int C, int TM, int IN, int OUT>
 inline cudaError_t fwd_launch(const FwdArgs& a, int grid, cudaStream_t st) {
-    if constexpr (CarryShape<C, TM, IN>::OK) {
+    if constexpr (carry_preferred<C, TM, IN>()) {
         using S = CarryShape<C, TM, IN>;
         pfb_fwd_carry_kernel<C, TM, IN, OUT><<<grid, S::NT, S::SMEM, st>>>(a);
     } else if constexpr (PushShape<C, TM, IN>::OK && !PPF_NO_PUSH) {
