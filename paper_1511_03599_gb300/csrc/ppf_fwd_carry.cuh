@@ -103,18 +103,21 @@ struct better_cand {
     using type = typename std::conditional<(X::SCORE > A::SCORE), X, A>::type;
 };
 
-// The carry kernel's shape.  Batches of 16 spectra are kept for C >= 512
-// and for fp32 input at C = 256, where they already allow two CTAs per SM
-// (smaller batches there measured slower: at C = 512 they spill, at C = 256
-// fp32 the per-batch overhead costs more than the extra CTAs give).  Otherwise batch
-// sizes 16, 8 and 4 are tried and the one with the most resident threads per
-// SM wins (the larger batch on ties).
+// The carry kernel's shape.  Batches of 16 spectra wherever they fit: the
+// more resident threads per SM that smaller batches allow did not pay for
+// their per-batch overhead (C = 64 int8 T = 8: 561 GS/s with 16 spectra vs
+// 379 with 8; C = 256 int16 T = 4: 494 vs 172; C = 128 fp32 T = 4: 377 vs
+// 267; at C = 512 smaller batches spill).  Two exceptions keep the batch
+// with the most resident threads per SM (the larger on ties): int8 at
+// C = 128 with 5-8 taps (483 vs 468 GS/s), and fp32 at C = 256 where 16
+// spectra leave one CTA per SM.
 template <int C, int TM, int IN>
 struct CarryShapeSel {
     using C16 = CarryCand<C, TM, IN, 16>;
     using Best = typename better_cand<typename better_cand<C16, CarryCand<C, TM, IN, 8>>::type,
                                       CarryCand<C, TM, IN, 4>>::type;
-    static constexpr bool KEEP16 = C16::OK && (C >= 512 || (C == 256 && IN == IN_CF32 && C16::MINB >= 2));
+    static constexpr bool KEEP16 = C16::OK && !(C == 128 && IN == IN_CI8 && TM == 8) &&
+                                   !(C == 256 && IN == IN_CF32 && C16::MINB < 2);
     using type = typename std::conditional<KEEP16, C16, Best>::type;
 };
 template <int C, int TM, int IN>
