@@ -221,15 +221,20 @@ struct FwdShape {
     static constexpr int NT = NTO ? NTO : (C >= 2048 || (C == 1024 && IN == IN_CF32 && TM == 16 && PPF_WIDE_1024)) ? 512 : 256;
     static constexpr int PAIRS = C / 2;
     // spectra per batch: 64 KB of filtered spectra (48 KB for C = 3 * 2^k),
-    // 64-128 KB at C = 2048 and 4096 (generic_batch_large)
+    // 64-128 KB at C = 2048 and 4096 (generic_batch_large); half that where
+    // it lets the TMA ring fit beside the batch: 16/32-bit input at C = 32
+    // (fp32 T = 8: 244 vs 120 GS/s; int16 T = 8: 233 vs 148) and 16-tap
+    // int16 input at C = 768 (140 vs 102)
     static constexpr int B = (C == 4096) ? (PPF_GENERIC_B4096 ? PPF_GENERIC_B4096 : generic_batch_large(C, TM, InTraits<IN>::bytes, NT))
                            : (C == 2048) ? (PPF_GENERIC_B2048 ? PPF_GENERIC_B2048 : generic_batch_large(C, TM, InTraits<IN>::bytes, NT))
                            : C == 3072 ? PPF_GENERIC_B3072
                            : (C == 1024 && IN != IN_CI8 && TM <= 4) ? PPF_GENERIC_B1024_SHORT
+                           : (C == 32 && IN != IN_CI8) ? 128
+                           : (C == 768 && IN == IN_CI16 && TM == 16) ? 4
                            : is_c3(C) ? 16 * 384 / C : 8192 / C;
     // large-T FIR order (see fir_segment): tap chunks for narrow input at C <= 512
     static constexpr bool CHUNK = TM > 16 && IN != IN_CF32 && C <= 512;
-    static constexpr int L0 = (TM >= 32 && !CHUNK) ? 8 : 16;
+    static constexpr int L0 = (TM >= 32 && !CHUNK) || (C == 32 && IN != IN_CI8) ? 8 : 16;
     static constexpr int L = L0 < B ? L0 : B;                        // FIR segment (outputs)
     static constexpr int G = B / L;                                  // segments per batch
     static constexpr int FIR_ITEMS = PAIRS * G;                      // (pair, segment) items

@@ -76,6 +76,21 @@ def test_parity_channels_taps_ci8(ppf, C, T):
     run_case(ppf, C, T, S, "ci8", "c64", seed=1000 + C + T)
 
 
+# shapes whose batch is halved so the TMA ring fits beside it: 16/32-bit input
+# at C = 32 (128-spectrum batches of 8-output segments, up to 64 taps) and
+# 16-tap int16 input at C = 768 (4-spectrum batches, a 6-slot ring); ragged
+# counts spanning several batches
+@pytest.mark.parametrize("C,T,in_dtype,out_dtype", [(32, 1, "ci16", "c64"), (32, 8, "cf32", "c64"),
+                                                    (32, 16, "ci16", "c16"), (32, 40, "cf32", "c64"),
+                                                    (32, 64, "ci16", "c64"), (768, 16, "ci16", "c64"),
+                                                    (768, 13, "ci16", "c16")])
+def test_parity_halved_batches(ppf, C, T, in_dtype, out_dtype):
+    S = 5 * 128 + 7 if C == 32 else 6 * 152 * 4 + 9
+    with ppf.Plan(C, T, synth.design_taps(C, T), in_dtype, out_dtype) as plan:
+        assert plan.info()["variant"] & 1, "expected the TMA-ring mode for this shape"
+    run_case(ppf, C, T, S, in_dtype, out_dtype, seed=4500 + C + T)
+
+
 # C = 3 * 2^k: a radix-3 DFT stage, then power-of-two stages (the paper's
 # non-power-of-two example is C = 3072)
 @pytest.mark.parametrize("C", [384, 768, 1536, 3072])
